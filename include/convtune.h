@@ -1,0 +1,274 @@
+/*
+ * convtune — auto-tuned direct single-channel 2D correlation for GB300 (sm_103a).
+ *
+ * The library implements the tunable 2D convolution kernel and the empirical
+ * tuning loop studied in "Bringing Auto-tuning to HIP: Analysis of Tuning
+ * Impact and Difficulty on AMD and Nvidia GPUs" (Lurati et al., 2024):
+ *   - the kernel and its tunable parameters: Sec. 5 "Benchmark kernels",
+ *     Table 1 (block_size_x/y, tile_size_x/y, use_shmem) and the loop-unrolling
+ *     parameter of Sec. 3;
+ *   - compile-and-benchmark of every configuration, timed by events recorded
+ *     before and after the kernel: Sec. 3;
+ *   - search strategies over the space: Sec. 3 ("optimization algorithms");
+ *   - analysis of a full timing table (tuning impact = optimum / median,
+ *     Sec. 4; proportion of centrality, Eq. 1; portability, Eqs. 2-3).
+ *
+ * Operation (the paper gives no formula; the library computes a "valid"
+ * cross-correlation, no filter flip, no padding):
+ *     out[y][x] = sum_{i<filter_h} sum_{j<filter_w} in[y+i][x+j] * f[i][j]
+ *     0 <= y < out_h, 0 <= x < out_w;  in is (out_h+filter_h-1) rows by
+ *     (out_w+filter_w-1) columns.
+ * Arithmetic: FP32 fused multiply-add per tap, taps added in (i, j) order,
+ * identical for every configuration.  BF16 problems store image and filter in
+ * BF16 and widen them exactly to FP32; the output is FP32.
+ *
+ * Conventions for every call:
+ *   - No call aborts or exits.  Each returns a ct_status; ct_last_error()
+ *     returns a thread-local message for the last failing call of the thread.
+ *   - Device pointers ("d_") are CUDA device (or managed) memory owned by the
+ *     caller; host pointers ("h_") are ordinary host memory owned by the caller
+ *     and are not retained after the call returns.
+ *   - Layout: images are row-major with a row pitch in ELEMENTS; every row
+ *     must start on a 16-byte boundary (pitch * element size a multiple of 16,
+ *     base pointer 16-byte aligned).  The image buffer must hold in_h full
+ *     rows of in_pitch elements; the output buffer out_h rows of out_pitch.
+ *     Elements between the valid width and the pitch are never used for a
+ *     stored output (they may hold anything, including NaN).
+ *   - Streams are CUDA runtime streams (cudaStream_t) passed as void*; NULL is
+ *     the legacy default stream.
+ */
+#ifndef CONVTUNE_H
+#define CONVTUNE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CT_API __attribute__((visibility("default")))
+#else
+#define CT_API
+#endif
+
+typedef enum {
+    CT_OK = 0,
+    CT_ERR_INVALID_ARG = -1,    /* null pointer, bad size, pitch or alignment */
+    CT_ERR_INVALID_CONFIG = -2, /* config outside the launchable set (threads, smem, tiles) */
+    CT_ERR_COMPILE = -3,        /* NVRTC failed for this variant */
+    CT_ERR_LAUNCH = -4,         /* the launch was rejected (resources) */
+    CT_ERR_CUDA = -5,           /* any other CUDA runtime error */
+    CT_ERR_OOM = -6,            /* a host or device allocation failed */
+    CT_ERR_TIMEOUT = -7,        /* a bounded wait gave up */
+    CT_ERR_UNSUPPORTED = -8     /* no device, or not an sm_103 device */
+} ct_status;
+
+typedef enum { CT_F32 = 0, CT_BF16 = 1 } ct_dtype;
+
+/* One correlation problem.  in_w = out_w + filter_w - 1, in_h = out_h + filter_h - 1.
+ * 1 <= filter_w, filter_h <= CT_MAX_FILTER; 0 <= out_w, out_h (a zero size is a
+ * no-op); in_pitch >= in_w, out_pitch >= out_w, both in elements. */
+typedef struct {
+    int32_t out_w, out_h;
+    int32_t filter_w, filter_h;
+    int64_t in_pitch, out_pitch;
+    int32_t dtype; /* ct_dtype */
+    int32_t reserved;
+} ct_problem;
+
+#define CT_MAX_FILTER 32
+
+/* One point of the search space (Table 1 names: block_size_x, block_size_y,
+ * tile_size_x, tile_size_y, use_shmem; unroll is Sec. 3's loop unrolling).
+ * block_x * block_y <= 1024; 1 <= tile_x, tile_y <= 16; use_smem in {0, 1};
+ * unroll in {0, 1}.  With use_smem = 1, block_x * tile_x must be a multiple
+ * of 4 (the staged tile starts on a 16-byte boundary). */
+typedef struct {
+    int32_t block_x, block_y;
+    int32_t tile_x, tile_y;
+    int32_t use_smem, unroll;
+} ct_config;
+
+/* Per-variant build facts (from the NVRTC/ptxas log and the launch shape). */
+typedef struct {
+    int32_t regs;          /* registers per thread */
+    int32_t spill_bytes;   /* spill stores + loads reported by ptxas */
+    int32_t smem_bytes;    /* dynamic shared memory per block */
+    int32_t cubin_bytes;
+    double compile_ms;     /* 0 when served from a cache */
+    int32_t from_cache;    /* 1: memory or disk cache hit */
+    int32_t reserved;
+} ct_variant_info;
+
+/* ---- library and device ---------------------------------------------- */
+
+CT_API const char* ct_version(void);
+/* Thread-local message of the last failing call on this thread ("" if none). */
+CT_API const char* ct_last_error(void);
+
+typedef struct {
+    char name[128];
+    int32_t sm_count, cc_major, cc_minor;
+    int32_t smem_optin_bytes;   /* max dynamic shared memory per block */
+    int32_t l2_bytes;
+    int32_t clock_max_khz;      /* 0 if unknown */
+    int32_t reserved;
+} ct_device_info;
+
+/* Current device facts; CT_ERR_UNSUPPORTED when no CUDA device is usable. */
+CT_API ct_status ct_device_query(ct_device_info* out);
+
+/* Directory for the on-disk cubin cache (NULL or "" disables it).  The
+ * default is taken from the CONVTUNE_CACHE_DIR environment variable. */
+CT_API ct_status ct_set_cache_dir(const char* dir);
+
+/* Drops every loaded variant (modules are unloaded on the current device). */
+CT_API ct_status ct_clear_cache(void);
+
+/* ---- configurations and variants -------------------------------------- */
+
+/* The baseline configuration: one output per thread, 32 x 8 threads,
+ * global-memory reads, rolled filter-row loop. */
+CT_API ct_status ct_default_config(const ct_problem* p, ct_config* out);
+
+/* Checks that (p, c) is launchable: argument ranges, threads per block and
+ * the shared-memory tile against smem_limit_bytes (<= 0: the current
+ * device's opt-in limit, or 232448 when there is no device).  Returns
+ * CT_ERR_INVALID_CONFIG or CT_ERR_INVALID_ARG with a message otherwise. */
+CT_API ct_status ct_check_config(const ct_problem* p, const ct_config* c, int32_t smem_limit_bytes);
+
+/* Compiles (or finds in a cache) the variant for (p, c) without loading it.
+ * Runs on a machine without a GPU: NVRTC targets sm_103a directly. */
+CT_API ct_status ct_compile(const ct_problem* p, const ct_config* c, ct_variant_info* info);
+
+/* ---- the correlation ---------------------------------------------------- */
+
+/* out = correlate(image, filter) with configuration c, enqueued on stream.
+ * d_image: in_h x in_pitch elements of p->dtype.  h_filter: filter_h x
+ * filter_w row-major host array (float for CT_F32, raw bf16 bits uint16_t for
+ * CT_BF16); it is copied into the launch before return.  d_out: out_h x
+ * out_pitch floats.  Asynchronous with respect to the host; the first call
+ * for a variant compiles and loads it (synchronously).  Errors:
+ * CT_ERR_INVALID_ARG / CT_ERR_INVALID_CONFIG (nothing enqueued),
+ * CT_ERR_COMPILE, CT_ERR_LAUNCH, CT_ERR_CUDA, CT_ERR_UNSUPPORTED. */
+CT_API ct_status ct_conv2d(const ct_problem* p, const ct_config* c, const void* d_image,
+                           const void* h_filter, float* d_out, void* stream);
+
+/* End-to-end form of ct_conv2d for host-resident data: copies h_image to
+ * d_image_ws, runs the correlation into d_out_ws and copies the result to
+ * h_out, all on stream, then synchronises the stream.  The workspaces are
+ * caller-owned device buffers of the sizes ct_conv2d needs; h_image and
+ * h_out should be pinned for the copies to run at full speed. */
+CT_API ct_status ct_conv2d_host(const ct_problem* p, const ct_config* c, const void* h_image,
+                                const void* h_filter, float* h_out, void* d_image_ws,
+                                float* d_out_ws, void* stream);
+
+/* ---- search spaces ------------------------------------------------------- */
+
+typedef struct ct_space ct_space;
+
+/* Built-in spaces (parameter order block_x, block_y, tile_x, tile_y,
+ * use_smem, unroll; canonical index = position in the Cartesian product,
+ * first parameter outermost):
+ *   "small": block_x {16,32,64,128} x block_y {1,2,4,8} x tile {1,2}^2 x
+ *            smem {0,1} x unroll {0,1}                      = 256 configs
+ *   "full":  block_x {16..256 pow2} x block_y {1..16 pow2} x tile {1..8}^2 x
+ *            smem {0,1} x unroll {0,1}                      = 6400 raw
+ *   "paper": Table 1's convolution values: block_x 16k (k = 1..16) x
+ *            block_y {1,2,4,8,16} x tile {1..4}^2 x smem {0,1} x unroll {0,1}
+ * Restrictions (applied per problem): threads per block <= 1024 and the
+ * shared-memory tile within the device limit. */
+CT_API ct_status ct_space_builtin(const char* name, ct_space** out);
+/* A space from JSON: {"block_x":[...], "block_y":[...], "tile_x":[...],
+ * "tile_y":[...], "use_smem":[...], "unroll":[...]} (missing keys take the
+ * single value of the default configuration). */
+CT_API ct_status ct_space_from_json(const char* json, ct_space** out);
+CT_API void ct_space_free(ct_space* s);
+/* Number of raw points and of points valid for p (smem_limit as in
+ * ct_check_config). */
+CT_API ct_status ct_space_count(const ct_space* s, const ct_problem* p, int32_t smem_limit_bytes,
+                                int64_t* n_raw, int64_t* n_valid);
+/* Writes up to cap valid configurations for p, in canonical order, with their
+ * canonical indices (either output may be NULL); *n gets the total. */
+CT_API ct_status ct_space_enumerate(const ct_space* s, const ct_problem* p, int32_t smem_limit_bytes,
+                                    ct_config* cfgs, int64_t* indices, int64_t cap, int64_t* n);
+
+/* ---- tuning --------------------------------------------------------------- */
+
+typedef enum { CT_BRUTE = 0, CT_RANDOM = 1, CT_ANNEAL = 2 } ct_strategy;
+
+typedef struct {
+    uint64_t seed;            /* strategy randomness and scratch inputs */
+    double sample_fraction;   /* budget of RANDOM/ANNEAL as a fraction of the valid configs (0: 0.10) */
+    int32_t max_evals;        /* > 0: overrides the budget */
+    int32_t repeats;          /* timed launches per config (0: 7) */
+    int32_t warmup;           /* untimed launches before timing (0: 1) */
+    int32_t flush_l2;         /* 1: overwrite L2 before every timed launch */
+    int32_t compile_threads;  /* 0: one per host core */
+    int32_t graph_below_us;   /* kernels shorter than this are timed as a graph of
+                                 back-to-back launches (0: 50 us; < 0: never) */
+    const char* cache_dir;    /* cubin cache for this run (NULL: library setting) */
+    const char* resume_path;  /* JSONL table: rows found there are not re-measured,
+                                 new rows are appended (NULL: none) */
+} ct_tune_opts;
+
+/* One row of a timing table. */
+typedef struct {
+    ct_config cfg;
+    int64_t index;            /* canonical index in the space */
+    int32_t status;           /* ct_status of compile/launch for this config */
+    int32_t n;                /* timed samples */
+    double t_med_ms, t_min_ms, t_std_ms;
+    double gflops;            /* 2 * out_w * out_h * filter_w * filter_h / t_med */
+    int32_t regs, spill_bytes, smem_bytes;
+    int32_t eval_order;       /* 0-based order in which the strategy measured it */
+    double compile_ms;
+} ct_row;
+
+typedef struct {
+    int32_t strategy;         /* ct_strategy */
+    int32_t n_rows;           /* configurations measured (or failed) */
+    int64_t n_valid_space;    /* valid configurations of the space for the problem */
+    int64_t best_row;         /* row index of the optimum (-1 if none) */
+    double wall_ms;           /* whole ct_tune call */
+    double compile_wall_ms;   /* wall time the benchmark loop waited on compiles */
+    double compile_cpu_ms;    /* sum of NVRTC compile times */
+    double bench_ms;          /* wall time spent launching and timing */
+} ct_table_info;
+
+typedef struct ct_table ct_table;
+
+/* Tunes p over space s with strategy st: every visited configuration is
+ * compiled (in parallel on host threads), launched, timed with CUDA events on
+ * a private stream (median of opts->repeats), and recorded.  Failing
+ * configurations become rows with a non-zero status and tuning continues.
+ * d_image / d_out may be NULL, in which case the library allocates scratch
+ * buffers filled from opts->seed and frees them before return; h_filter may
+ * be NULL (seeded filter).  Synchronous.  *best_out gets the fastest config
+ * (ties: lower canonical index); *table_out a library-owned table (free with
+ * ct_table_free). */
+CT_API ct_status ct_tune(const ct_problem* p, const ct_space* s, ct_strategy st,
+                         const ct_tune_opts* opts, const void* d_image, const void* h_filter,
+                         float* d_out, ct_config* best_out, ct_table** table_out);
+
+/* The same strategies driven by a given timing landscape instead of the GPU:
+ * the "measurement" of the configuration with canonical index k is
+ * times_ms[k] (k < n_times; NaN or <= 0 marks a failing configuration).
+ * Needs no device.  Used to study and test strategies offline. */
+CT_API ct_status ct_tune_replay(const ct_problem* p, const ct_space* s, ct_strategy st,
+                                const ct_tune_opts* opts, const double* times_ms, int64_t n_times,
+                                ct_config* best_out, ct_table** table_out);
+
+CT_API int64_t ct_table_size(const ct_table* t);
+CT_API ct_status ct_table_row(const ct_table* t, int64_t i, ct_row* out);
+CT_API ct_status ct_table_info_get(const ct_table* t, ct_table_info* out);
+/* Writes the table as JSON lines (one object per row). */
+CT_API ct_status ct_table_write(const ct_table* t, const char* path);
+CT_API void ct_table_free(ct_table* t);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CONVTUNE_H */

@@ -1,0 +1,417 @@
+"""convtune — auto-tuned direct 2D correlation for GB300, Python binding.
+
+A thin ctypes layer over ``libconvtune.so`` (``include/convtune.h``): it only
+marshals arguments.  Every step of the correlation runs in the library's CUDA
+kernels; PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the library is missing or cannot load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libconvtune.so")
+
+CT_OK = 0
+STATUS = {0: "CT_OK", -1: "CT_ERR_INVALID_ARG", -2: "CT_ERR_INVALID_CONFIG", -3: "CT_ERR_COMPILE",
+          -4: "CT_ERR_LAUNCH", -5: "CT_ERR_CUDA", -6: "CT_ERR_OOM", -7: "CT_ERR_TIMEOUT", -8: "CT_ERR_UNSUPPORTED"}
+CT_F32, CT_BF16 = 0, 1
+STRATEGIES = {"brute": 0, "random": 1, "anneal": 2}
+MAX_FILTER = 32
+
+i32, i64, u64, dbl, vp, cp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double,
+                              ctypes.c_void_p, ctypes.c_char_p)
+
+
+class CTError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("out_w", i32), ("out_h", i32), ("filter_w", i32), ("filter_h", i32),
+                ("in_pitch", i64), ("out_pitch", i64), ("dtype", i32), ("reserved", i32)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("block_x", i32), ("block_y", i32), ("tile_x", i32), ("tile_y", i32),
+                ("use_smem", i32), ("unroll", i32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+    def as_tuple(self):
+        return tuple(int(getattr(self, k)) for k, _ in self._fields_)
+
+    def __repr__(self):
+        return "Config(%s)" % ", ".join(f"{k}={v}" for k, v in self.as_dict().items())
+
+    def __eq__(self, other):
+        return isinstance(other, Config) and self.as_tuple() == other.as_tuple()
+
+    def __hash__(self):
+        return hash(self.as_tuple())
+
+
+class VariantInfo(ctypes.Structure):
+    _fields_ = [("regs", i32), ("spill_bytes", i32), ("smem_bytes", i32), ("cubin_bytes", i32),
+                ("compile_ms", dbl), ("from_cache", i32), ("reserved", i32)]
+
+
+class DeviceInfo(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 128), ("sm_count", i32), ("cc_major", i32), ("cc_minor", i32),
+                ("smem_optin_bytes", i32), ("l2_bytes", i32), ("clock_max_khz", i32), ("reserved", i32)]
+
+
+class TuneOpts(ctypes.Structure):
+    _fields_ = [("seed", u64), ("sample_fraction", dbl), ("max_evals", i32), ("repeats", i32),
+                ("warmup", i32), ("flush_l2", i32), ("compile_threads", i32), ("graph_below_us", i32),
+                ("cache_dir", cp), ("resume_path", cp)]
+
+
+class Row(ctypes.Structure):
+    _fields_ = [("cfg", Config), ("index", i64), ("status", i32), ("n", i32), ("t_med_ms", dbl),
+                ("t_min_ms", dbl), ("t_std_ms", dbl), ("gflops", dbl), ("regs", i32), ("spill_bytes", i32),
+                ("smem_bytes", i32), ("eval_order", i32), ("compile_ms", dbl)]
+
+
+class TableInfo(ctypes.Structure):
+    _fields_ = [("strategy", i32), ("n_rows", i32), ("n_valid_space", i64), ("best_row", i64),
+                ("wall_ms", dbl), ("compile_wall_ms", dbl), ("compile_cpu_ms", dbl), ("bench_ms", dbl)]
+
+
+P = ctypes.POINTER
+_SIGS = {
+    "ct_version": (cp, []),
+    "ct_last_error": (cp, []),
+    "ct_device_query": (i32, [P(DeviceInfo)]),
+    "ct_set_cache_dir": (i32, [cp]),
+    "ct_clear_cache": (i32, []),
+    "ct_default_config": (i32, [P(Problem), P(Config)]),
+    "ct_check_config": (i32, [P(Problem), P(Config), i32]),
+    "ct_compile": (i32, [P(Problem), P(Config), P(VariantInfo)]),
+    "ct_conv2d": (i32, [P(Problem), P(Config), vp, vp, vp, vp]),
+    "ct_conv2d_host": (i32, [P(Problem), P(Config), vp, vp, vp, vp, vp, vp]),
+    "ct_space_builtin": (i32, [cp, P(vp)]),
+    "ct_space_from_json": (i32, [cp, P(vp)]),
+    "ct_space_free": (None, [vp]),
+    "ct_space_count": (i32, [vp, P(Problem), i32, P(i64), P(i64)]),
+    "ct_space_enumerate": (i32, [vp, P(Problem), i32, P(Config), P(i64), i64, P(i64)]),
+    "ct_tune": (i32, [P(Problem), vp, i32, P(TuneOpts), vp, vp, vp, P(Config), P(vp)]),
+    "ct_tune_replay": (i32, [P(Problem), vp, i32, P(TuneOpts), P(dbl), i64, P(Config), P(vp)]),
+    "ct_table_size": (i64, [vp]),
+    "ct_table_row": (i32, [vp, i64, P(Row)]),
+    "ct_table_info_get": (i32, [vp, P(TableInfo)]),
+    "ct_table_write": (i32, [vp, cp]),
+    "ct_table_free": (None, [vp]),
+}
+EXPORTED = tuple(_SIGS)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libconvtune.so is not built ({LIB_PATH}); run "
+                                  "paper_2407_11488_gb300.build.build()")
+            try:
+                import torch  # noqa: F401  (shares its CUDA runtime with the library)
+            except ImportError:
+                pass
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def lib():
+    """The loaded ctypes library (raises if it is missing)."""
+    return _load()
+
+
+def _check(status: int):
+    if status != CT_OK:
+        raise CTError(status, _load().ct_last_error().decode(errors="replace"))
+
+
+def version() -> str:
+    return _load().ct_version().decode()
+
+
+def device_query() -> DeviceInfo:
+    d = DeviceInfo()
+    _check(_load().ct_device_query(ctypes.byref(d)))
+    return d
+
+
+def set_cache_dir(path):
+    _check(_load().ct_set_cache_dir(path.encode() if path else None))
+
+
+def clear_cache():
+    _check(_load().ct_clear_cache())
+
+
+def config(block_x=32, block_y=8, tile_x=1, tile_y=1, use_smem=0, unroll=0) -> Config:
+    return Config(block_x, block_y, tile_x, tile_y, use_smem, unroll)
+
+
+def default_config() -> Config:
+    c = Config()
+    _check(_load().ct_default_config(None, ctypes.byref(c)))
+    return c
+
+
+def round_up(v, m):
+    return (v + m - 1) // m * m
+
+
+def make_problem(out_w, out_h, filter_w, filter_h, *, in_pitch=None, out_pitch=None, dtype=CT_F32) -> Problem:
+    if in_pitch is None:
+        in_pitch = round_up(out_w + filter_w - 1, 8 if dtype == CT_BF16 else 4)
+    if out_pitch is None:
+        out_pitch = round_up(max(out_w, 1), 4)
+    return Problem(out_w, out_h, filter_w, filter_h, in_pitch, out_pitch, dtype, 0)
+
+
+def check_config(problem: Problem, cfg: Config, smem_limit: int = 0):
+    _check(_load().ct_check_config(ctypes.byref(problem), ctypes.byref(cfg), smem_limit))
+
+
+def compile_variant(problem: Problem, cfg: Config) -> dict:
+    """Compiles the variant (NVRTC → sm_103a cubin) without loading it; works
+    without a GPU.  Returns the ptxas facts."""
+    info = VariantInfo()
+    _check(_load().ct_compile(ctypes.byref(problem), ctypes.byref(cfg), ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in VariantInfo._fields_ if k != "reserved"}
+
+
+# ------------------------------------------------------------ correlation ---
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float32:
+        return CT_F32
+    if t.dtype == torch.bfloat16:
+        return CT_BF16
+    raise TypeError(f"image dtype {t.dtype} is not float32 or bfloat16")
+
+
+def _filter_bytes(filt, dtype):
+    """Host copy of the filter as float32 (CT_F32) or raw bf16 bits (CT_BF16)."""
+    import torch
+    if isinstance(filt, torch.Tensor):
+        f = filt.detach().cpu()
+        if dtype == CT_BF16:
+            if f.dtype != torch.bfloat16:
+                raise TypeError("a bf16 problem needs a bfloat16 filter")
+            arr = f.contiguous().view(torch.int16).numpy().view(np.uint16)
+        else:
+            arr = f.to(torch.float32).contiguous().numpy()
+    else:
+        arr = np.ascontiguousarray(filt, dtype=np.uint16 if dtype == CT_BF16 else np.float32)
+    if arr.ndim != 2:
+        raise ValueError("filter must be 2-D (filter_h, filter_w)")
+    return np.ascontiguousarray(arr)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def problem_for(image, filt, in_w=None, out_pitch=None) -> Problem:
+    """The Problem for an image tensor of shape (in_h, in_pitch) whose first
+    ``in_w`` columns are valid (default: all of them) and a (fh, fw) filter."""
+    fh, fw = int(filt.shape[0]), int(filt.shape[1])
+    in_h, pitch = int(image.shape[0]), int(image.stride(0))
+    if in_w is None:
+        in_w = int(image.shape[1])
+    out_w, out_h = in_w - fw + 1, in_h - fh + 1
+    if out_w < 0 or out_h < 0:
+        raise ValueError("filter larger than image")
+    if out_pitch is None:
+        out_pitch = round_up(max(out_w, 1), 4)
+    return Problem(out_w, out_h, fw, fh, pitch, out_pitch, _dtype_code(image), 0)
+
+
+def conv2d(image, filt, cfg: Config | None = None, *, in_w=None, out=None, stream=None):
+    """Valid cross-correlation of a device image with a host filter.
+
+    image: CUDA tensor (in_h, in_pitch), float32 or bfloat16, rows 16-byte
+    aligned; filt: (fh, fw) host array/tensor; out: optional CUDA float32
+    tensor (out_h, out_pitch).  Enqueued on ``stream`` (default: torch's
+    current stream).  Returns the (out_h, out_w) view of the output."""
+    import torch
+    if not isinstance(image, torch.Tensor) or not image.is_cuda:
+        raise TypeError("image must be a CUDA tensor")
+    if image.stride(1) != 1:
+        raise ValueError("image rows must be contiguous")
+    p = problem_for(image, filt, in_w)
+    fb = _filter_bytes(filt, p.dtype)
+    if out is None:
+        out = torch.empty((p.out_h, p.out_pitch), dtype=torch.float32, device=image.device)
+    else:
+        if out.dtype != torch.float32 or not out.is_cuda or out.stride(1) != 1:
+            raise TypeError("out must be a CUDA float32 tensor with contiguous rows")
+        p.out_pitch = out.stride(0)
+        if out.shape[0] < p.out_h or out.shape[1] < p.out_w:
+            raise ValueError("out is too small")
+    cfg = cfg or default_config()
+    _check(_load().ct_conv2d(ctypes.byref(p), ctypes.byref(cfg), ctypes.c_void_p(image.data_ptr()),
+                             fb.ctypes.data_as(vp), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out[:p.out_h, :p.out_w]
+
+
+def conv2d_raw(problem: Problem, cfg: Config, d_image: int, h_filter: np.ndarray, d_out: int, stream: int = 0):
+    """ct_conv2d on raw device addresses (for timing loops)."""
+    _check(_load().ct_conv2d(ctypes.byref(problem), ctypes.byref(cfg), ctypes.c_void_p(d_image),
+                             h_filter.ctypes.data_as(vp), ctypes.c_void_p(d_out), ctypes.c_void_p(stream)))
+
+
+def conv2d_host(problem: Problem, cfg: Config, h_image, h_filter: np.ndarray, h_out, d_image_ws, d_out_ws,
+                stream=None):
+    """End-to-end: host image in, host output out (copies on the stream, then
+    a synchronisation).  All arrays are torch tensors (host ones pinned)."""
+    _check(_load().ct_conv2d_host(ctypes.byref(problem), ctypes.byref(cfg), ctypes.c_void_p(h_image.data_ptr()),
+                                  h_filter.ctypes.data_as(vp), ctypes.c_void_p(h_out.data_ptr()),
+                                  ctypes.c_void_p(d_image_ws.data_ptr()), ctypes.c_void_p(d_out_ws.data_ptr()),
+                                  _stream_ptr(stream)))
+
+
+# ------------------------------------------------------------------ spaces ---
+class Space:
+    """A search space handle (built-in name or JSON text)."""
+
+    def __init__(self, spec="small"):
+        h = vp()
+        if spec.lstrip().startswith("{"):
+            _check(_load().ct_space_from_json(spec.encode(), ctypes.byref(h)))
+        else:
+            _check(_load().ct_space_builtin(spec.encode(), ctypes.byref(h)))
+        self.handle = h
+        self.spec = spec
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ct_space_free(self.handle)
+            self.handle = None
+
+    def count(self, problem: Problem, smem_limit: int = 0):
+        raw, valid = i64(), i64()
+        _check(_load().ct_space_count(self.handle, ctypes.byref(problem), smem_limit, ctypes.byref(raw),
+                                      ctypes.byref(valid)))
+        return raw.value, valid.value
+
+    def enumerate(self, problem: Problem, smem_limit: int = 0):
+        n = i64()
+        _check(_load().ct_space_enumerate(self.handle, ctypes.byref(problem), smem_limit, None, None, 0,
+                                          ctypes.byref(n)))
+        cfgs = (Config * n.value)()
+        idx = (i64 * n.value)()
+        _check(_load().ct_space_enumerate(self.handle, ctypes.byref(problem), smem_limit, cfgs, idx, n.value,
+                                          ctypes.byref(n)))
+        return [(int(idx[i]), cfgs[i]) for i in range(n.value)]
+
+
+def _space(space):
+    return space if isinstance(space, Space) else Space(space)
+
+
+# ------------------------------------------------------------------ tuning ---
+@dataclass
+class Table:
+    rows: list
+    info: dict
+    best: Config | None
+
+    def valid(self):
+        return [r for r in self.rows if r["status"] == 0 and math.isfinite(r["t_med_ms"])]
+
+
+def _row_dict(r: Row) -> dict:
+    d = {k: getattr(r, k) for k, _ in Row._fields_ if k != "cfg"}
+    d["cfg"] = Config(*r.cfg.as_tuple())
+    d.update(r.cfg.as_dict())
+    return d
+
+
+def _collect(t, best, write_path=None) -> Table:
+    L = _load()
+    try:
+        if write_path:
+            _check(L.ct_table_write(t, write_path.encode()))
+        info = TableInfo()
+        _check(L.ct_table_info_get(t, ctypes.byref(info)))
+        rows = []
+        for i in range(L.ct_table_size(t)):
+            r = Row()
+            _check(L.ct_table_row(t, i, ctypes.byref(r)))
+            rows.append(_row_dict(r))
+        infod = {k: getattr(info, k) for k, _ in TableInfo._fields_}
+        return Table(rows, infod, best)
+    finally:
+        L.ct_table_free(t)
+
+
+def _opts(seed=0, sample_fraction=0.0, max_evals=0, repeats=0, warmup=0, flush_l2=False, compile_threads=0,
+          graph_below_us=0, cache_dir=None, resume_path=None):
+    return TuneOpts(seed, sample_fraction, max_evals, repeats, warmup, int(flush_l2), compile_threads,
+                    graph_below_us, cache_dir.encode() if cache_dir else None,
+                    resume_path.encode() if resume_path else None)
+
+
+def tune(problem: Problem, space="small", strategy="brute", *, image=None, filt=None, out=None,
+         write_path=None, **opts) -> Table:
+    """ct_tune: compile, launch and time every configuration the strategy
+    visits on the GPU; returns the timing table with its best config."""
+    sp = _space(space)
+    o = _opts(**opts)
+    fb = _filter_bytes(filt, problem.dtype) if filt is not None else None
+    best = Config()
+    t = vp()
+    st = _load().ct_tune(ctypes.byref(problem), sp.handle, STRATEGIES[strategy], ctypes.byref(o),
+                         ctypes.c_void_p(image.data_ptr()) if image is not None else None,
+                         fb.ctypes.data_as(vp) if fb is not None else None,
+                         ctypes.c_void_p(out.data_ptr()) if out is not None else None,
+                         ctypes.byref(best), ctypes.byref(t))
+    if t.value:
+        table = _collect(t, best if st == CT_OK else None, write_path)
+        if st != CT_OK:
+            raise CTError(st, _load().ct_last_error().decode(errors="replace"))
+        return table
+    _check(st)
+    raise CTError(-5, "ct_tune returned no table")
+
+
+def tune_replay(problem: Problem, space, strategy, times_ms, **opts) -> Table:
+    """The strategies over a given landscape: times_ms[k] is the time of the
+    configuration with canonical index k (NaN/<=0: failing)."""
+    sp = _space(space)
+    o = _opts(**opts)
+    arr = np.ascontiguousarray(times_ms, dtype=np.float64)
+    best = Config()
+    t = vp()
+    st = _load().ct_tune_replay(ctypes.byref(problem), sp.handle, STRATEGIES[strategy], ctypes.byref(o),
+                                arr.ctypes.data_as(P(dbl)), len(arr), ctypes.byref(best), ctypes.byref(t))
+    if t.value:
+        return _collect(t, best if st == CT_OK else None)
+    _check(st)
+    raise CTError(-5, "ct_tune_replay returned no table")

@@ -1,0 +1,226 @@
+// The C-ABI of libconvtune.so (declared in include/convtune.h).
+#include "ct_internal.hpp"
+
+#include <cstdio>
+#include <cstring>
+
+using namespace ct;
+
+extern "C" {
+
+CT_API const char* ct_version(void) { return "convtune 0.1 (sm_103a, NVRTC variants)"; }
+
+CT_API const char* ct_last_error(void) { return last_error(); }
+
+CT_API ct_status ct_device_query(ct_device_info* out)
+{
+    if (!out) return fail(CT_ERR_INVALID_ARG, "out is NULL");
+    memset(out, 0, sizeof *out);
+    int n = 0, dev = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return fail(CT_ERR_UNSUPPORTED, "no CUDA device is available");
+    }
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    snprintf(out->name, sizeof out->name, "%.127s", prop.name);
+    out->sm_count = prop.multiProcessorCount;
+    out->cc_major = prop.major;
+    out->cc_minor = prop.minor;
+    out->smem_optin_bytes = (int32_t)prop.sharedMemPerBlockOptin;
+    out->l2_bytes = prop.l2CacheSize;
+    int clk = 0;
+    if (cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, dev) != cudaSuccess) {
+        cudaGetLastError();
+        clk = 0;
+    }
+    out->clock_max_khz = clk;
+    return CT_OK;
+}
+
+CT_API ct_status ct_set_cache_dir(const char* dir)
+{
+    cache_dir_setting() = dir ? dir : "";
+    return CT_OK;
+}
+
+CT_API ct_status ct_clear_cache(void)
+{
+    clear_variants();
+    return CT_OK;
+}
+
+CT_API ct_status ct_default_config(const ct_problem* p, ct_config* out)
+{
+    (void)p;
+    if (!out) return fail(CT_ERR_INVALID_ARG, "out is NULL");
+    *out = ct_config{32, 8, 1, 1, 0, 0};
+    return CT_OK;
+}
+
+CT_API ct_status ct_check_config(const ct_problem* p, const ct_config* c, int32_t smem_limit_bytes)
+{
+    ct_status s = check_problem(p);
+    if (s != CT_OK) return s;
+    if (!c) return fail(CT_ERR_INVALID_ARG, "config is NULL");
+    return check_config(*p, *c, smem_limit_bytes);
+}
+
+CT_API ct_status ct_compile(const ct_problem* p, const ct_config* c, ct_variant_info* info)
+{
+    ct_status s = check_problem(p);
+    if (s != CT_OK) return s;
+    if (!c) return fail(CT_ERR_INVALID_ARG, "config is NULL");
+    if ((s = check_config(*p, *c, kDefaultSmemLimit)) != CT_OK) return s;
+    VariantPtr v = get_variant(VariantKey{*c, p->filter_w, p->filter_h, p->dtype});
+    if (info) {
+        memset(info, 0, sizeof *info);
+        info->regs = v->regs;
+        info->spill_bytes = v->spill_bytes;
+        info->smem_bytes = (int32_t)v->smem;
+        info->cubin_bytes = (int32_t)v->cubin.size();
+        info->compile_ms = v->compile_ms;
+        info->from_cache = v->from_cache ? 1 : 0;
+    }
+    if (v->status != CT_OK) return fail((ct_status)v->status, "%s", v->error.c_str());
+    return CT_OK;
+}
+
+CT_API ct_status ct_conv2d(const ct_problem* p, const ct_config* c, const void* d_image, const void* h_filter,
+                           float* d_out, void* stream)
+{
+    ct_status s = check_problem(p);
+    if (s != CT_OK) return s;
+    if (!c) return fail(CT_ERR_INVALID_ARG, "config is NULL");
+    if ((s = check_buffers(*p, d_image, h_filter, d_out)) != CT_OK) return s;
+    if ((s = require_device()) != CT_OK) return s;
+    if ((s = check_config(*p, *c, 0)) != CT_OK) return s;
+    if (p->out_w == 0 || p->out_h == 0) return CT_OK;
+    VariantPtr v = get_variant(VariantKey{*c, p->filter_w, p->filter_h, p->dtype});
+    if (v->status != CT_OK) return fail((ct_status)v->status, "%s", v->error.c_str());
+    return launch_variant(*v, *p, d_image, h_filter, d_out, (cudaStream_t)stream);
+}
+
+CT_API ct_status ct_conv2d_host(const ct_problem* p, const ct_config* c, const void* h_image, const void* h_filter,
+                                float* h_out, void* d_image_ws, float* d_out_ws, void* stream)
+{
+    ct_status s = check_problem(p);
+    if (s != CT_OK) return s;
+    if (!c) return fail(CT_ERR_INVALID_ARG, "config is NULL");
+    if (p->out_w == 0 || p->out_h == 0) return CT_OK;
+    if (!h_image || !h_out) return fail(CT_ERR_INVALID_ARG, "host image or output is NULL");
+    if ((s = check_buffers(*p, d_image_ws, h_filter, d_out_ws)) != CT_OK) return s;
+    if ((s = require_device()) != CT_OK) return s;
+    if ((s = check_config(*p, *c, 0)) != CT_OK) return s;
+    VariantPtr v = get_variant(VariantKey{*c, p->filter_w, p->filter_h, p->dtype});
+    if (v->status != CT_OK) return fail((ct_status)v->status, "%s", v->error.c_str());
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t in_bytes = (size_t)(in_h(*p) * p->in_pitch * elem_size(p->dtype));
+    const size_t out_bytes = (size_t)(p->out_h * p->out_pitch * 4);
+    cudaError_t e = cudaMemcpyAsync(d_image_ws, h_image, in_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(H2D image)");
+    if ((s = launch_variant(*v, *p, d_image_ws, h_filter, d_out_ws, st)) != CT_OK) return s;
+    if ((e = cudaMemcpyAsync(h_out, d_out_ws, out_bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(D2H output)");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return CT_OK;
+}
+
+// ---------------------------------------------------------------- spaces ---
+CT_API ct_status ct_space_builtin(const char* name, ct_space** out)
+{
+    if (!name || !out) return fail(CT_ERR_INVALID_ARG, "name and out must be non-NULL");
+    auto* s = new ct_space();
+    if (!builtin_space(name, s->s)) {
+        delete s;
+        return fail(CT_ERR_INVALID_ARG, "unknown built-in space '%s' (small, full, paper)", name);
+    }
+    *out = s;
+    return CT_OK;
+}
+
+CT_API ct_status ct_space_from_json(const char* json, ct_space** out)
+{
+    if (!json || !out) return fail(CT_ERR_INVALID_ARG, "json and out must be non-NULL");
+    auto* s = new ct_space();
+    std::string err;
+    if (!space_from_json(json, s->s, err)) {
+        delete s;
+        return fail(CT_ERR_INVALID_ARG, "space JSON: %s", err.c_str());
+    }
+    *out = s;
+    return CT_OK;
+}
+
+CT_API void ct_space_free(ct_space* s) { delete s; }
+
+CT_API ct_status ct_space_count(const ct_space* s, const ct_problem* p, int32_t smem_limit_bytes, int64_t* n_raw,
+                                int64_t* n_valid)
+{
+    ct_status st = check_problem(p);
+    if (st != CT_OK) return st;
+    if (!s) return fail(CT_ERR_INVALID_ARG, "space is NULL");
+    const int lim = smem_limit_bytes > 0 ? smem_limit_bytes : device_smem_limit();
+    if (n_raw) *n_raw = s->s.raw_size();
+    if (n_valid) *n_valid = (int64_t)enumerate_valid(s->s, *p, lim).size();
+    return CT_OK;
+}
+
+CT_API ct_status ct_space_enumerate(const ct_space* s, const ct_problem* p, int32_t smem_limit_bytes, ct_config* cfgs,
+                                    int64_t* indices, int64_t cap, int64_t* n)
+{
+    ct_status st = check_problem(p);
+    if (st != CT_OK) return st;
+    if (!s) return fail(CT_ERR_INVALID_ARG, "space is NULL");
+    const int lim = smem_limit_bytes > 0 ? smem_limit_bytes : device_smem_limit();
+    std::vector<Entry> v = enumerate_valid(s->s, *p, lim);
+    for (int64_t i = 0; i < (int64_t)v.size() && i < cap; ++i) {
+        if (cfgs) cfgs[i] = v[(size_t)i].cfg;
+        if (indices) indices[i] = v[(size_t)i].index;
+    }
+    if (n) *n = (int64_t)v.size();
+    return CT_OK;
+}
+
+// ---------------------------------------------------------------- tuning ---
+CT_API ct_status ct_tune(const ct_problem* p, const ct_space* s, ct_strategy st, const ct_tune_opts* opts,
+                         const void* d_image, const void* h_filter, float* d_out, ct_config* best_out,
+                         ct_table** table_out)
+{
+    return tune_gpu(p, s, st, opts, d_image, h_filter, d_out, best_out, table_out);
+}
+
+CT_API ct_status ct_tune_replay(const ct_problem* p, const ct_space* s, ct_strategy st, const ct_tune_opts* opts,
+                                const double* times_ms, int64_t n_times, ct_config* best_out, ct_table** table_out)
+{
+    return tune_replay(p, s, st, opts, times_ms, n_times, best_out, table_out);
+}
+
+CT_API int64_t ct_table_size(const ct_table* t) { return t ? (int64_t)t->rows.size() : 0; }
+
+CT_API ct_status ct_table_row(const ct_table* t, int64_t i, ct_row* out)
+{
+    if (!t || !out) return fail(CT_ERR_INVALID_ARG, "table and out must be non-NULL");
+    if (i < 0 || i >= (int64_t)t->rows.size()) return fail(CT_ERR_INVALID_ARG, "row %lld out of range", (long long)i);
+    *out = t->rows[(size_t)i];
+    return CT_OK;
+}
+
+CT_API ct_status ct_table_info_get(const ct_table* t, ct_table_info* out)
+{
+    if (!t || !out) return fail(CT_ERR_INVALID_ARG, "table and out must be non-NULL");
+    *out = t->info;
+    return CT_OK;
+}
+
+CT_API ct_status ct_table_write(const ct_table* t, const char* path)
+{
+    if (!t || !path) return fail(CT_ERR_INVALID_ARG, "table and path must be non-NULL");
+    return write_table(*t, path, t->tag, false);
+}
+
+CT_API void ct_table_free(ct_table* t) { delete t; }
+
+}  // extern "C"

@@ -1,0 +1,265 @@
+// Direct single-channel 2D correlation, one tunable variant per compilation.
+//
+// This source is compiled at run time by NVRTC straight to an sm_103a cubin
+// (one cubin per point of the search space and filter size), the way an
+// empirical auto-tuner compiles and benchmarks each configuration of a
+// tunable kernel (Sec. 3 "Design and Implementation"; the tunable parameters
+// of the 2D convolution kernel are Table 1's block_size_x/y, tile_size_x/y,
+// use_shmem, plus the loop-unrolling switch of Sec. 3).
+//
+// Computes the valid cross-correlation
+//     out[y][x] = sum_{i<FH} sum_{j<FW} in[y+i][x+j] * f[i][j]
+// in FP32 with one fused multiply-add per tap.  Every variant adds the taps of
+// one output in the same order (i ascending, then j ascending), so all points
+// of the space give bit-identical results.
+//
+// Compile-time parameters (macros):
+//   CT_BX, CT_BY   thread-block shape (threads in x and y)
+//   CT_TX, CT_TY   outputs per thread in x and y (register tile)
+//   CT_SMEM        0: each thread reads its input window from global memory
+//                     (through L1);
+//                  1: the block stages its input tile plus halo in shared
+//                     memory with 16-byte vector loads, then reads windows
+//                     from there
+//   CT_UNROLL      1: fully unrolled; input rows slide through a register
+//                     window and each row feeds every output row that uses it;
+//                  0: the loop over filter rows stays rolled
+//   CT_FW, CT_FH   filter width and height
+//   CT_DTYPE       0: FP32 image; 1: BF16 image (widened to FP32 on load)
+//
+// Layout contract (checked by the host before launch): row pitches are in
+// elements and make every row start on a 16-byte boundary; the image buffer
+// holds in_h full rows of in_pitch elements; the filter taps travel by value
+// in the kernel's parameter block (constant bank), so FFMAs take them as
+// uniform operands with no load instruction.
+
+#ifndef CT_DTYPE
+#define CT_DTYPE 0
+#endif
+
+#ifdef CT_INJECT_COMPILE_ERROR
+#error "compile failure requested through CT_INJECT_COMPILE_ERROR"
+#endif
+
+typedef long long ct_i64;
+typedef unsigned int ct_u32;
+
+#if CT_DTYPE == 0
+typedef float ct_in_t;
+#else
+typedef unsigned short ct_in_t;
+#endif
+
+struct CtParams {
+    const ct_in_t* in;
+    float* out;
+    ct_i64 in_pitch;
+    ct_i64 out_pitch;
+    int out_w, out_h;
+    int in_w, in_h;
+    float f[CT_FH * CT_FW];
+};
+
+#define CT_NT (CT_BX * CT_BY)
+#define CT_WW (CT_TX + CT_FW - 1)
+#define CT_TILE_W (CT_BX * CT_TX)
+#define CT_TILE_H (CT_BY * CT_TY)
+#define CT_HALO_W (CT_TILE_W + CT_FW - 1)
+#define CT_HALO_H (CT_TILE_H + CT_FH - 1)
+#define CT_SW (((CT_HALO_W + 3) / 4) * 4)
+
+#if CT_TX % 4 == 0
+#define CT_VW 4
+#elif CT_TX % 2 == 0
+#define CT_VW 2
+#else
+#define CT_VW 1
+#endif
+#define CT_WWV (((CT_WW + CT_VW - 1) / CT_VW) * CT_VW)
+
+__device__ __forceinline__ float ct_bf16(unsigned short h)
+{
+    return __uint_as_float(((ct_u32)h) << 16);
+}
+
+// Loads VW consecutive input elements starting at p (aligned to VW elements).
+template <int VW>
+__device__ __forceinline__ void ct_ldg(float* w, const ct_in_t* __restrict__ p)
+{
+#if CT_DTYPE == 0
+    if (VW == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    } else if (VW == 2) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        w[0] = v.x; w[1] = v.y;
+    } else {
+        w[0] = __ldg(p);
+    }
+#else
+    if (VW == 4) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+        w[0] = __uint_as_float(v.x << 16); w[1] = __uint_as_float(v.x & 0xffff0000u);
+        w[2] = __uint_as_float(v.y << 16); w[3] = __uint_as_float(v.y & 0xffff0000u);
+    } else if (VW == 2) {
+        const ct_u32 v = __ldg(reinterpret_cast<const unsigned int*>(p));
+        w[0] = __uint_as_float(v << 16); w[1] = __uint_as_float(v & 0xffff0000u);
+    } else {
+        w[0] = ct_bf16(__ldg(p));
+    }
+#endif
+}
+
+// One input row of the thread's window: columns gx .. gx+CT_WWV-1 of row gy.
+// Chunks that start at or beyond in_w (or rows beyond in_h) read as zero; a
+// chunk that starts inside the row may run into the row's padding, which
+// only feeds outputs at x >= out_w (never stored).
+__device__ __forceinline__ void ct_row_global(float (&w)[CT_WWV], const CtParams& p, int gy, int gx)
+{
+    if (gy < p.in_h) {
+        const ct_in_t* __restrict__ row = p.in + (ct_i64)gy * p.in_pitch + gx;
+#pragma unroll
+        for (int k = 0; k < CT_WWV; k += CT_VW) {
+            if (gx + k < p.in_w) {
+                ct_ldg<CT_VW>(w + k, row + k);
+            } else {
+#pragma unroll
+                for (int e = 0; e < CT_VW; ++e) w[k + e] = 0.0f;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < CT_WWV; ++k) w[k] = 0.0f;
+    }
+}
+
+__device__ __forceinline__ void ct_row_shared(float (&w)[CT_WWV], const float* __restrict__ s)
+{
+#pragma unroll
+    for (int k = 0; k < CT_WWV; k += CT_VW) {
+        if (CT_VW == 4) {
+            const float4 v = *reinterpret_cast<const float4*>(s + k);
+            w[k] = v.x; w[k + 1] = v.y; w[k + 2] = v.z; w[k + 3] = v.w;
+        } else if (CT_VW == 2) {
+            const float2 v = *reinterpret_cast<const float2*>(s + k);
+            w[k] = v.x; w[k + 1] = v.y;
+        } else {
+            w[k] = s[k];
+        }
+    }
+}
+
+extern "C" __global__ void __launch_bounds__(CT_NT)
+ct_corr2d(const __grid_constant__ CtParams p)
+{
+    const int lx = threadIdx.x * CT_TX;
+    const int ly = threadIdx.y * CT_TY;
+    const int gx0 = blockIdx.x * CT_TILE_W;
+    const int gy0 = blockIdx.y * CT_TILE_H;
+    const int gx = gx0 + lx;
+    const int gy = gy0 + ly;
+
+#if CT_SMEM
+    extern __shared__ float4 ct_smem4[];
+    float* sm = reinterpret_cast<float*>(ct_smem4);
+    {
+        // Stage rows gy0 .. gy0+HALO_H-1, columns gx0 .. gx0+SW-1 in 4-element
+        // chunks (16 bytes for FP32, 8 for BF16).  gx0 is a multiple of 16.
+        constexpr int CH = CT_SW / 4;
+        constexpr int NCH = CT_HALO_H * CH;
+        const int tid = threadIdx.y * CT_BX + threadIdx.x;
+#pragma unroll 4
+        for (int idx = tid; idx < NCH; idx += CT_NT) {
+            const int r = idx / CH;
+            const int c = (idx - r * CH) * 4;
+            const int yy = gy0 + r, xx = gx0 + c;
+            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (yy < p.in_h && xx < p.in_w) {
+                const ct_in_t* src = p.in + (ct_i64)yy * p.in_pitch + xx;
+#if CT_DTYPE == 0
+                v = __ldg(reinterpret_cast<const float4*>(src));
+#else
+                const uint2 u = __ldg(reinterpret_cast<const uint2*>(src));
+                v = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                                __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+#endif
+            }
+            *reinterpret_cast<float4*>(sm + r * CT_SW + c) = v;
+        }
+    }
+    __syncthreads();
+#define CT_LOAD_ROW(w, r) ct_row_shared(w, sm + (ly + (r)) * CT_SW + lx)
+#else
+#define CT_LOAD_ROW(w, r) ct_row_global(w, p, gy + (r), gx)
+#endif
+
+    float acc[CT_TY][CT_TX];
+#pragma unroll
+    for (int ty = 0; ty < CT_TY; ++ty)
+#pragma unroll
+        for (int tx = 0; tx < CT_TX; ++tx) acc[ty][tx] = 0.0f;
+
+#if CT_UNROLL
+    // Input row r feeds output rows ty with filter row i = r - ty.
+#pragma unroll
+    for (int r = 0; r < CT_TY + CT_FH - 1; ++r) {
+        float w[CT_WWV];
+        CT_LOAD_ROW(w, r);
+#pragma unroll
+        for (int ty = 0; ty < CT_TY; ++ty) {
+            const int i = r - ty;
+            if (i >= 0 && i < CT_FH) {
+#pragma unroll
+                for (int j = 0; j < CT_FW; ++j) {
+                    const float fv = p.f[i * CT_FW + j];
+#pragma unroll
+                    for (int tx = 0; tx < CT_TX; ++tx)
+                        acc[ty][tx] = fmaf(w[tx + j], fv, acc[ty][tx]);
+                }
+            }
+        }
+    }
+#else
+#pragma unroll 1
+    for (int i = 0; i < CT_FH; ++i) {
+#pragma unroll
+        for (int ty = 0; ty < CT_TY; ++ty) {
+            float w[CT_WWV];
+            CT_LOAD_ROW(w, ty + i);
+#pragma unroll
+            for (int j = 0; j < CT_FW; ++j) {
+                const float fv = p.f[i * CT_FW + j];
+#pragma unroll
+                for (int tx = 0; tx < CT_TX; ++tx)
+                    acc[ty][tx] = fmaf(w[tx + j], fv, acc[ty][tx]);
+            }
+        }
+    }
+#endif
+#undef CT_LOAD_ROW
+
+#pragma unroll
+    for (int ty = 0; ty < CT_TY; ++ty) {
+        const int y = gy + ty;
+        if (y < p.out_h) {
+            float* __restrict__ orow = p.out + (ct_i64)y * p.out_pitch + gx;
+#if CT_TX % 4 == 0
+#pragma unroll
+            for (int k = 0; k < CT_TX; k += 4) {
+                if (gx + k + 3 < p.out_w) {
+                    *reinterpret_cast<float4*>(orow + k) =
+                        make_float4(acc[ty][k], acc[ty][k + 1], acc[ty][k + 2], acc[ty][k + 3]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (gx + k + e < p.out_w) orow[k + e] = acc[ty][k + e];
+                }
+            }
+#else
+#pragma unroll
+            for (int tx = 0; tx < CT_TX; ++tx)
+                if (gx + tx < p.out_w) orow[tx] = acc[ty][tx];
+#endif
+        }
+    }
+}

@@ -1,0 +1,763 @@
+// Runner and strategies: compile pool, event-timed benchmark of one variant,
+// brute force / random sampling / simulated annealing, timing tables.
+#include "ct_internal.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <limits>
+#include <set>
+#include <sstream>
+
+namespace ct {
+
+// ---------------------------------------------------------- compile pool ---
+CompilePool::CompilePool(int nthreads, std::string cache_dir) : cache_dir_(std::move(cache_dir))
+{
+    if (nthreads <= 0) nthreads = (int)std::max(1u, std::thread::hardware_concurrency());
+    for (int i = 0; i < nthreads; ++i) threads_.emplace_back([this] { worker(); });
+}
+
+CompilePool::~CompilePool()
+{
+    {
+        std::lock_guard<std::mutex> g(mu_);
+        stop_ = true;
+        for (auto& q : queue_) q.second->set_value(nullptr);
+        queue_.clear();
+    }
+    cv_.notify_all();
+    for (auto& t : threads_) t.join();
+}
+
+std::shared_future<VariantPtr> CompilePool::request(const VariantKey& k)
+{
+    std::lock_guard<std::mutex> g(mu_);
+    auto it = futures_.find(k.packed());
+    if (it != futures_.end()) return it->second;
+    auto pr = std::make_shared<std::promise<VariantPtr>>();
+    auto fut = pr->get_future().share();
+    futures_[k.packed()] = fut;
+    queue_.emplace_back(k, pr);
+    cv_.notify_one();
+    return fut;
+}
+
+void CompilePool::forget(const VariantKey& k)
+{
+    std::lock_guard<std::mutex> g(mu_);
+    futures_.erase(k.packed());
+}
+
+void CompilePool::worker()
+{
+    for (;;) {
+        std::pair<VariantKey, std::shared_ptr<std::promise<VariantPtr>>> job;
+        {
+            std::unique_lock<std::mutex> g(mu_);
+            cv_.wait(g, [this] { return stop_ || !queue_.empty(); });
+            if (stop_) return;
+            job = queue_.front();
+            queue_.pop_front();
+        }
+        job.second->set_value(compile_variant(job.first, cache_dir_));
+    }
+}
+
+// ------------------------------------------------------------- measuring ---
+struct Measure {
+    int status = CT_OK;
+    int n = 0;
+    double med = NAN, mn = NAN, sd = NAN;
+    int regs = 0, spill = 0;
+    int64_t smem = 0;
+    double compile_ms = 0.0;
+};
+
+static void summarize(std::vector<double>& t, Measure& m)
+{
+    std::sort(t.begin(), t.end());
+    const size_t n = t.size();
+    m.n = (int)n;
+    if (!n) return;
+    m.med = (n % 2) ? t[n / 2] : 0.5 * (t[n / 2 - 1] + t[n / 2]);
+    m.mn = t[0];
+    double mean = 0;
+    for (double x : t) mean += x;
+    mean /= (double)n;
+    double ss = 0;
+    for (double x : t) ss += (x - mean) * (x - mean);
+    m.sd = n > 1 ? std::sqrt(ss / (double)(n - 1)) : 0.0;
+}
+
+class Evaluator {
+public:
+    virtual ~Evaluator() = default;
+    virtual void prefetch(const Entry&) {}
+    virtual Measure eval(const Entry& e) = 0;
+    double compile_wait_ms = 0, compile_cpu_ms = 0, bench_ms = 0;
+    bool abort = false;   // set after an unrecoverable device error
+};
+
+class ReplayEvaluator : public Evaluator {
+public:
+    ReplayEvaluator(const double* t, int64_t n) : t_(t), n_(n) {}
+    Measure eval(const Entry& e) override
+    {
+        Measure m;
+        const double v = e.index < n_ ? t_[e.index] : NAN;
+        if (!(v > 0.0) || !std::isfinite(v)) {
+            m.status = CT_ERR_LAUNCH;
+            return m;
+        }
+        m.n = 1;
+        m.med = m.mn = v;
+        m.sd = 0.0;
+        return m;
+    }
+private:
+    const double* t_;
+    int64_t n_;
+};
+
+struct TimeOpts {
+    int repeats = 7, warmup = 1, flush_l2 = 0;
+    double graph_below_ms = 0.05;
+};
+
+class GpuEvaluator : public Evaluator {
+public:
+    GpuEvaluator(const ct_problem& p, const TimeOpts& o, const void* d_image, const void* h_filter, float* d_out,
+                 CompilePool& pool, void* flush_buf, int64_t flush_bytes, cudaStream_t stream)
+        : p_(p), o_(o), img_(d_image), filt_(h_filter), out_(d_out), pool_(pool), flush_(flush_buf),
+          flush_bytes_(flush_bytes), s_(stream)
+    {
+        for (auto& e : ev_) cudaEventCreate(&e);
+    }
+    ~GpuEvaluator() override
+    {
+        for (auto& e : ev_) cudaEventDestroy(e);
+    }
+    VariantKey key(const Entry& e) const { return VariantKey{e.cfg, p_.filter_w, p_.filter_h, p_.dtype}; }
+    void prefetch(const Entry& e) override { pool_.request(key(e)); }
+
+    Measure eval(const Entry& e) override
+    {
+        Measure m;
+        const VariantKey k = key(e);
+        const double t0 = now_ms();
+        VariantPtr v = pool_.request(k).get();
+        compile_wait_ms += now_ms() - t0;
+        pool_.forget(k);
+        if (!v) {
+            m.status = CT_ERR_COMPILE;
+            return m;
+        }
+        m.regs = v->regs;
+        m.spill = v->spill_bytes;
+        m.smem = v->smem;
+        m.compile_ms = v->compile_ms;
+        compile_cpu_ms += v->compile_ms;
+        if (v->status != CT_OK) {
+            m.status = v->status;
+            return m;
+        }
+        const double b0 = now_ms();
+        m.status = time_variant(*v, m);
+        bench_ms += now_ms() - b0;
+        if (m.status == CT_OK && (!best_ || m.med < best_t_)) {
+            best_ = v;
+            best_t_ = m.med;
+        } else {
+            unload_variant(*v);
+        }
+        return m;
+    }
+    VariantPtr best() const { return best_; }
+    ct_status fatal = CT_OK;
+
+private:
+    ct_status launch(Variant& v) { return launch_variant(v, p_, img_, filt_, out_, s_); }
+
+    int time_variant(Variant& v, Measure& m)
+    {
+        ct_status s = load_variant(v);
+        if (s != CT_OK) return s == CT_ERR_CUDA ? CT_ERR_LAUNCH : s;
+        for (int w = 0; w < std::max(1, o_.warmup); ++w) {
+            s = launch(v);
+            if (s != CT_OK) {
+                cudaGetLastError();
+                return CT_ERR_LAUNCH;
+            }
+        }
+        cudaError_t e = cudaStreamSynchronize(s_);
+        if (e != cudaSuccess) {
+            fatal = cuda_fail(e, "kernel execution during tuning");
+            abort = true;
+            return CT_ERR_CUDA;
+        }
+        // one probe launch decides between single-launch and graph timing
+        cudaEventRecord(ev_[0], s_);
+        launch(v);
+        cudaEventRecord(ev_[1], s_);
+        if ((e = cudaEventSynchronize(ev_[1])) != cudaSuccess) {
+            fatal = cuda_fail(e, "kernel execution during tuning");
+            abort = true;
+            return CT_ERR_CUDA;
+        }
+        float probe = 0.f;
+        cudaEventElapsedTime(&probe, ev_[0], ev_[1]);
+        std::vector<double> t;
+        if (probe < o_.graph_below_ms) {
+            const int K = std::min(1000, std::max(2, (int)std::ceil(0.5 / std::max(1e-4, (double)probe))));
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            if ((e = cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamBeginCapture"), CT_ERR_CUDA;
+            bool ok = true;
+            for (int i = 0; i < K && ok; ++i) ok = launch(v) == CT_OK;
+            e = cudaStreamEndCapture(s_, &g);
+            if (!ok || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                return CT_ERR_LAUNCH;
+            }
+            e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate"), CT_ERR_CUDA;
+            cudaGraphLaunch(ge, s_);   // warm the graph
+            for (int r = 0; r < o_.repeats; ++r) {
+                cudaEventRecord(ev_[2 * (r % 16)], s_);
+                cudaGraphLaunch(ge, s_);
+                cudaEventRecord(ev_[2 * (r % 16) + 1], s_);
+                if (r % 16 == 15 || r == o_.repeats - 1) {
+                    cudaEventSynchronize(ev_[2 * (r % 16) + 1]);
+                    for (int q = r - r % 16; q <= r; ++q) {
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, ev_[2 * (q % 16)], ev_[2 * (q % 16) + 1]);
+                        t.push_back((double)ms / K);
+                    }
+                }
+            }
+            cudaGraphExecDestroy(ge);
+        } else {
+            for (int r = 0; r < o_.repeats; ++r) {
+                if (o_.flush_l2 && flush_) launch_l2_flush(flush_, flush_bytes_, (uint32_t)r, s_);
+                cudaEventRecord(ev_[2 * (r % 16)], s_);
+                launch(v);
+                cudaEventRecord(ev_[2 * (r % 16) + 1], s_);
+                if (r % 16 == 15 || r == o_.repeats - 1) {
+                    cudaEventSynchronize(ev_[2 * (r % 16) + 1]);
+                    for (int q = r - r % 16; q <= r; ++q) {
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, ev_[2 * (q % 16)], ev_[2 * (q % 16) + 1]);
+                        t.push_back((double)ms);
+                    }
+                }
+            }
+        }
+        if ((e = cudaStreamSynchronize(s_)) != cudaSuccess) {
+            fatal = cuda_fail(e, "kernel execution during tuning");
+            abort = true;
+            return CT_ERR_CUDA;
+        }
+        summarize(t, m);
+        return CT_OK;
+    }
+
+    ct_problem p_;
+    TimeOpts o_;
+    const void* img_;
+    const void* filt_;
+    float* out_;
+    CompilePool& pool_;
+    void* flush_;
+    int64_t flush_bytes_;
+    cudaStream_t s_;
+    cudaEvent_t ev_[32];
+    VariantPtr best_;
+    double best_t_ = 0;
+};
+
+// ------------------------------------------------------------ table I/O ---
+static std::string problem_tag(const ct_problem& p)
+{
+    char b[96];
+    snprintf(b, sizeof b, "%dx%d/f%dx%d/%s", p.out_w, p.out_h, p.filter_w, p.filter_h,
+             p.dtype == CT_BF16 ? "bf16" : "f32");
+    return b;
+}
+
+static void fmt_num(std::ostringstream& os, double v)
+{
+    if (std::isfinite(v)) {
+        char b[64];
+        snprintf(b, sizeof b, "%.17g", v);
+        os << b;
+    } else {
+        os << "null";
+    }
+}
+
+static std::string row_json(const ct_row& r, const std::string& tag)
+{
+    std::ostringstream os;
+    os << "{\"problem\":\"" << tag << "\",\"index\":" << r.index;
+    for (int k = 0; k < 6; ++k) os << ",\"" << kParamNames[k] << "\":" << cfg_get(r.cfg, k);
+    os << ",\"status\":" << r.status << ",\"n\":" << r.n << ",\"t_med_ms\":";
+    fmt_num(os, r.t_med_ms);
+    os << ",\"t_min_ms\":";
+    fmt_num(os, r.t_min_ms);
+    os << ",\"t_std_ms\":";
+    fmt_num(os, r.t_std_ms);
+    os << ",\"gflops\":";
+    fmt_num(os, r.gflops);
+    os << ",\"regs\":" << r.regs << ",\"spill_bytes\":" << r.spill_bytes << ",\"smem_bytes\":" << r.smem_bytes
+       << ",\"eval_order\":" << r.eval_order << ",\"compile_ms\":";
+    fmt_num(os, r.compile_ms);
+    os << "}";
+    return os.str();
+}
+
+static bool json_num(const std::string& line, const char* name, double& v)
+{
+    std::string pat = std::string("\"") + name + "\":";
+    size_t pos = line.find(pat);
+    if (pos == std::string::npos) return false;
+    const char* s = line.c_str() + pos + pat.size();
+    if (!strncmp(s, "null", 4)) {
+        v = NAN;
+        return true;
+    }
+    char* end = nullptr;
+    v = strtod(s, &end);
+    return end != s;
+}
+
+// Rows of an earlier run of the same problem, keyed by the packed config.
+static std::unordered_map<uint64_t, Measure> read_resume(const char* path, const ct_problem& p)
+{
+    std::unordered_map<uint64_t, Measure> out;
+    if (!path || !*path) return out;
+    std::ifstream f(path);
+    if (!f) return out;
+    const std::string tag = "\"problem\":\"" + problem_tag(p) + "\"";
+    std::string line;
+    while (std::getline(f, line)) {
+        if (line.find(tag) == std::string::npos) continue;
+        ct_config c{};
+        double v = 0;
+        bool ok = true;
+        for (int k = 0; k < 6; ++k) {
+            ok = ok && json_num(line, kParamNames[k], v);
+            cfg_set(c, k, (int)v);
+        }
+        Measure m;
+        double st = 0, n = 0, r = 0, sp = 0, sm = 0, cm = 0;
+        ok = ok && json_num(line, "status", st) && json_num(line, "n", n) && json_num(line, "t_med_ms", m.med) &&
+             json_num(line, "t_min_ms", m.mn) && json_num(line, "t_std_ms", m.sd);
+        if (!ok) continue;
+        json_num(line, "regs", r);
+        json_num(line, "spill_bytes", sp);
+        json_num(line, "smem_bytes", sm);
+        json_num(line, "compile_ms", cm);
+        m.status = (int)st;
+        m.n = (int)n;
+        m.regs = (int)r;
+        m.spill = (int)sp;
+        m.smem = (int64_t)sm;
+        m.compile_ms = std::isfinite(cm) ? cm : 0.0;
+        out[VariantKey{c, p.filter_w, p.filter_h, p.dtype}.packed()] = m;
+    }
+    return out;
+}
+
+ct_status write_table(const ct_table& t, const char* path, const std::string& tag, bool append)
+{
+    FILE* f = fopen(path, append ? "a" : "w");
+    if (!f) return fail(CT_ERR_INVALID_ARG, "cannot open %s for writing", path);
+    for (const auto& r : t.rows) fprintf(f, "%s\n", row_json(r, tag).c_str());
+    fclose(f);
+    return CT_OK;
+}
+
+// ------------------------------------------------------------ strategies ---
+class Driver {
+public:
+    Driver(const ct_problem& p, const Space& s, const std::vector<Entry>& valid, Evaluator& ev,
+           std::unordered_map<uint64_t, Measure> resume, const char* append_path)
+        : p_(p), s_(s), valid_(valid), ev_(ev), resume_(std::move(resume)), tag_(problem_tag(p))
+    {
+        for (size_t i = 0; i < valid_.size(); ++i) pos_[valid_[i].index] = i;
+        if (append_path && *append_path) append_ = fopen(append_path, "a");
+    }
+    ~Driver()
+    {
+        if (append_) fclose(append_);
+    }
+
+    bool is_valid(int64_t idx) const { return pos_.count(idx) != 0; }
+    const Entry& entry(int64_t idx) const { return valid_[pos_.at(idx)]; }
+    bool visited(int64_t idx) const { return row_of_.count(idx) != 0; }
+    size_t n_rows() const { return rows.size(); }
+
+    void prefetch(const Entry& e)
+    {
+        if (!visited(e.index) && !resume_.count(VariantKey{e.cfg, p_.filter_w, p_.filter_h, p_.dtype}.packed()))
+            ev_.prefetch(e);
+    }
+
+    // Measures e once (memoised); returns its median time or +inf on failure.
+    double evaluate(const Entry& e, bool* fresh = nullptr)
+    {
+        auto it = row_of_.find(e.index);
+        if (fresh) *fresh = it == row_of_.end();
+        if (it != row_of_.end()) return objective(rows[it->second]);
+        Measure m;
+        auto rit = resume_.find(VariantKey{e.cfg, p_.filter_w, p_.filter_h, p_.dtype}.packed());
+        if (rit != resume_.end()) {
+            m = rit->second;
+        } else {
+            m = ev_.eval(e);
+        }
+        ct_row r{};
+        r.cfg = e.cfg;
+        r.index = e.index;
+        r.status = m.status;
+        r.n = m.n;
+        r.t_med_ms = m.status == CT_OK ? m.med : NAN;
+        r.t_min_ms = m.status == CT_OK ? m.mn : NAN;
+        r.t_std_ms = m.status == CT_OK ? m.sd : NAN;
+        r.gflops = m.status == CT_OK ? problem_flops(p_) / (m.med * 1e6) : 0.0;
+        r.regs = m.regs;
+        r.spill_bytes = m.spill;
+        r.smem_bytes = (int32_t)m.smem;
+        r.eval_order = (int32_t)rows.size();
+        r.compile_ms = m.compile_ms;
+        row_of_[e.index] = rows.size();
+        rows.push_back(r);
+        if (append_ && rit == resume_.end()) {
+            fprintf(append_, "%s\n", row_json(r, tag_).c_str());
+            fflush(append_);
+        }
+        return objective(r);
+    }
+
+    static double objective(const ct_row& r)
+    {
+        return r.status == CT_OK && std::isfinite(r.t_med_ms) ? r.t_med_ms : std::numeric_limits<double>::infinity();
+    }
+
+    std::vector<ct_row> rows;
+
+private:
+    const ct_problem& p_;
+    const Space& s_;
+    const std::vector<Entry>& valid_;
+    Evaluator& ev_;
+    std::unordered_map<uint64_t, Measure> resume_;
+    std::string tag_;
+    std::unordered_map<int64_t, size_t> pos_;
+    std::unordered_map<int64_t, size_t> row_of_;
+    FILE* append_ = nullptr;
+};
+
+static int64_t budget_of(const ct_tune_opts& o, int64_t n_valid)
+{
+    if (o.max_evals > 0) return std::min<int64_t>(o.max_evals, n_valid);
+    const double f = o.sample_fraction > 0 ? o.sample_fraction : 0.10;
+    return std::min<int64_t>(n_valid, std::max<int64_t>(1, (int64_t)std::ceil(f * (double)n_valid - 1e-9)));
+}
+
+static void run_list(Driver& d, const std::vector<Entry>& order, int window, const bool* stop)
+{
+    for (size_t i = 0; i < order.size(); ++i) {
+        for (size_t j = i; j < std::min(order.size(), i + (size_t)window); ++j) d.prefetch(order[j]);
+        d.evaluate(order[i]);
+        if (stop && *stop) return;
+    }
+}
+
+// Valid neighbours: one parameter moved by one step in its ordered value list.
+static std::vector<int64_t> neighbours(const Space& s, const Driver& d, const ct_config& c)
+{
+    std::vector<int64_t> out;
+    for (int k = 0; k < 6; ++k) {
+        const auto& vals = s.vals[k];
+        int pos = -1;
+        for (size_t j = 0; j < vals.size(); ++j)
+            if (vals[j] == cfg_get(c, k)) pos = (int)j;
+        for (int dlt : {-1, 1}) {
+            const int q = pos + dlt;
+            if (pos < 0 || q < 0 || q >= (int)vals.size()) continue;
+            ct_config n = c;
+            cfg_set(n, k, vals[q]);
+            const int64_t idx = s.index_of(n);
+            if (idx >= 0 && d.is_valid(idx)) out.push_back(idx);
+        }
+    }
+    return out;
+}
+
+// Simulated annealing over the valid configurations (neighbourhood as above),
+// objective normalised by the first measured time, temperature cooled
+// geometrically from 1 to 1e-3 over the evaluation budget, Metropolis
+// acceptance, restart from the best point after budget/10 fresh evaluations
+// without improvement, memoised measurements.
+static void run_anneal(Driver& d, const Space& s, const std::vector<Entry>& valid, int64_t budget, uint64_t seed,
+                       const bool* stop)
+{
+    Rng rng(seed ^ 0xA5A5A5A5ull);
+    const Entry* cur = &valid[rng.below(valid.size())];
+    double f_first = d.evaluate(*cur);
+    double f_cur = f_first;
+    const Entry* best = cur;
+    double f_best = f_cur;
+    const double T0 = 1.0, T1 = 1e-3;
+    const int64_t stall_limit = std::max<int64_t>(1, budget / 10);
+    int64_t stall = 0, idle = 0, steps = 0;
+    const int64_t max_steps = 200 * budget + 1000;
+    while ((int64_t)d.n_rows() < budget && steps++ < max_steps) {
+        if (stop && *stop) return;
+        if (!std::isfinite(f_first)) {
+            // the first point failed: normalise by the first success instead
+            const Entry* e = &valid[rng.below(valid.size())];
+            f_first = d.evaluate(*e);
+            cur = e;
+            f_cur = f_first;
+            if (f_cur < f_best) { best = cur; f_best = f_cur; }
+            continue;
+        }
+        std::vector<int64_t> nb = neighbours(s, d, cur->cfg);
+        bool all_seen = true;
+        for (int64_t i : nb)
+            if (!d.visited(i)) {
+                d.prefetch(d.entry(i));
+                all_seen = false;
+            }
+        const Entry* cand;
+        if (nb.empty() || (all_seen && idle > 2 * (int64_t)nb.size())) {
+            // stuck in an explored region: jump to a random unvisited point
+            std::vector<const Entry*> fresh;
+            for (const auto& e : valid)
+                if (!d.visited(e.index)) fresh.push_back(&e);
+            if (fresh.empty()) return;
+            cand = fresh[rng.below(fresh.size())];
+            idle = 0;
+        } else {
+            cand = &d.entry(nb[rng.below(nb.size())]);
+        }
+        bool fresh_eval = false;
+        const double f_c = d.evaluate(*cand, &fresh_eval);
+        idle = fresh_eval ? 0 : idle + 1;
+        const double T = T0 * std::pow(T1 / T0, std::min(1.0, (double)d.n_rows() / (double)budget));
+        const double delta = (f_c - f_cur) / f_first;
+        if (std::isfinite(f_c) && (delta < 0 || rng.uniform() < std::exp(-delta / T))) {
+            cur = cand;
+            f_cur = f_c;
+        }
+        if (f_c < f_best) {
+            best = cand;
+            f_best = f_c;
+            stall = 0;
+        } else if (fresh_eval && ++stall >= stall_limit) {
+            cur = best;
+            f_cur = f_best;
+            stall = 0;
+        }
+    }
+}
+
+static std::vector<Entry> random_sample(const std::vector<Entry>& valid, int64_t m, uint64_t seed)
+{
+    std::vector<size_t> idx(valid.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    Rng rng(seed);
+    std::vector<Entry> out;
+    for (int64_t i = 0; i < m; ++i) {
+        const size_t j = (size_t)i + (size_t)rng.below(idx.size() - (size_t)i);
+        std::swap(idx[(size_t)i], idx[j]);
+        out.push_back(valid[idx[(size_t)i]]);
+    }
+    return out;
+}
+
+static ct_status run_strategy(const ct_problem& p, const Space& s, ct_strategy st, const ct_tune_opts& o,
+                              const std::vector<Entry>& valid, Evaluator& ev, ct_table& t, int window)
+{
+    const bool* stop = &ev.abort;
+    t.tag = problem_tag(p);
+    Driver d(p, s, valid, ev, read_resume(o.resume_path, p), o.resume_path);
+    const int64_t budget = budget_of(o, (int64_t)valid.size());
+    if (st == CT_BRUTE) {
+        run_list(d, valid, window, stop);
+    } else if (st == CT_RANDOM) {
+        run_list(d, random_sample(valid, budget, o.seed), window, stop);
+    } else if (st == CT_ANNEAL) {
+        run_anneal(d, s, valid, budget, o.seed, stop);
+    } else {
+        return fail(CT_ERR_INVALID_ARG, "unknown strategy %d", (int)st);
+    }
+    t.rows = std::move(d.rows);
+    t.info.strategy = st;
+    t.info.n_rows = (int32_t)t.rows.size();
+    t.info.n_valid_space = (int64_t)valid.size();
+    t.info.best_row = -1;
+    for (size_t i = 0; i < t.rows.size(); ++i) {
+        const ct_row& r = t.rows[i];
+        if (r.status != CT_OK || !std::isfinite(r.t_med_ms)) continue;
+        if (t.info.best_row < 0) {
+            t.info.best_row = (int64_t)i;
+            continue;
+        }
+        const ct_row& b = t.rows[(size_t)t.info.best_row];
+        if (r.t_med_ms < b.t_med_ms || (r.t_med_ms == b.t_med_ms && r.index < b.index)) t.info.best_row = (int64_t)i;
+    }
+    t.info.compile_wall_ms = ev.compile_wait_ms;
+    t.info.compile_cpu_ms = ev.compile_cpu_ms;
+    t.info.bench_ms = ev.bench_ms;
+    return CT_OK;
+}
+
+static ct_tune_opts normalise(const ct_tune_opts* o)
+{
+    ct_tune_opts r{};
+    if (o) r = *o;
+    if (r.repeats <= 0) r.repeats = 7;
+    if (r.warmup <= 0) r.warmup = 1;
+    if (r.graph_below_us == 0) r.graph_below_us = 50;
+    return r;
+}
+
+ct_status tune_replay(const ct_problem* p, const ct_space* s, ct_strategy st, const ct_tune_opts* opts,
+                      const double* times, int64_t n_times, ct_config* best_out, ct_table** table_out)
+{
+    ct_status rc = check_problem(p);
+    if (rc != CT_OK) return rc;
+    if (!s || !times || !table_out) return fail(CT_ERR_INVALID_ARG, "space, times and table_out must be non-NULL");
+    const double t0 = now_ms();
+    ct_tune_opts o = normalise(opts);
+    std::vector<Entry> valid = enumerate_valid(s->s, *p, kDefaultSmemLimit);
+    if (valid.empty()) return fail(CT_ERR_INVALID_CONFIG, "no valid configuration in the space for this problem");
+    ReplayEvaluator ev(times, n_times);
+    auto* t = new ct_table();
+    rc = run_strategy(*p, s->s, st, o, valid, ev, *t, 1);
+    if (rc != CT_OK) {
+        delete t;
+        return rc;
+    }
+    t->info.wall_ms = now_ms() - t0;
+    if (best_out && t->info.best_row >= 0) *best_out = t->rows[(size_t)t->info.best_row].cfg;
+    *table_out = t;
+    if (t->info.best_row < 0) return fail(CT_ERR_LAUNCH, "every evaluated configuration failed");
+    return CT_OK;
+}
+
+ct_status tune_gpu(const ct_problem* p, const ct_space* s, ct_strategy st, const ct_tune_opts* opts,
+                   const void* d_image, const void* h_filter, float* d_out, ct_config* best_out, ct_table** table_out)
+{
+    ct_status rc = check_problem(p);
+    if (rc != CT_OK) return rc;
+    if (!s || !table_out) return fail(CT_ERR_INVALID_ARG, "space and table_out must be non-NULL");
+    if (p->out_w == 0 || p->out_h == 0) return fail(CT_ERR_INVALID_ARG, "cannot tune an empty problem");
+    if ((rc = require_device()) != CT_OK) return rc;
+    const double t0 = now_ms();
+    ct_tune_opts o = normalise(opts);
+    const int smem_limit = device_smem_limit();
+    std::vector<Entry> valid = enumerate_valid(s->s, *p, smem_limit);
+    if (valid.empty()) return fail(CT_ERR_INVALID_CONFIG, "no valid configuration in the space for this problem");
+
+    cudaStream_t stream = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+    void* img = nullptr;
+    float* out = nullptr;
+    void* flush = nullptr;
+    int64_t flush_bytes = 0;
+    std::vector<unsigned char> filt;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(stream);
+        if (!d_image && img) cudaFree(img);
+        if (!d_out && out) cudaFree(out);
+        if (flush) cudaFree(flush);
+        cudaStreamDestroy(stream);
+    };
+    const int es = elem_size(p->dtype);
+    if (d_image) {
+        img = const_cast<void*>(d_image);
+    } else {
+        if ((e = cudaMalloc(&img, (size_t)(in_h(*p) * p->in_pitch * es))) != cudaSuccess) {
+            cleanup();
+            return cuda_fail(e, "cudaMalloc(scratch image)");
+        }
+        cudaMemsetAsync(img, 0, (size_t)(in_h(*p) * p->in_pitch * es), stream);
+        launch_fill_uniform(img, p->dtype, in_h(*p), in_w(*p), p->in_pitch, o.seed, 0, stream);
+    }
+    if (d_out) {
+        out = d_out;
+    } else if ((e = cudaMalloc((void**)&out, (size_t)(p->out_h * p->out_pitch * 4))) != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "cudaMalloc(scratch output)");
+    }
+    if (!h_filter) {
+        const int n = p->filter_w * p->filter_h;
+        filt.resize((size_t)n * 4);
+        const uint64_t start = (uint64_t)(in_w(*p) * in_h(*p));
+        for (int i = 0; i < n; ++i) {
+            const uint64_t u = splitmix64_at(o.seed, start + (uint64_t)i);
+            const float v = (float)((double)(int64_t)(u >> 40) * 0x1p-23 - 1.0);
+            if (p->dtype == CT_F32) {
+                memcpy(&filt[(size_t)i * 4], &v, 4);
+            } else {
+                uint32_t b;
+                memcpy(&b, &v, 4);
+                b += 0x7fffu + ((b >> 16) & 1u);
+                const uint16_t h = (uint16_t)(b >> 16);
+                memcpy(&filt[(size_t)i * 2], &h, 2);
+            }
+        }
+        h_filter = filt.data();
+    }
+    if (o.flush_l2) {
+        int dev = 0, l2 = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+        flush_bytes = 2 * (int64_t)std::max(l2, 64 << 20);
+        if ((e = cudaMalloc(&flush, (size_t)flush_bytes)) != cudaSuccess) {
+            cleanup();
+            return cuda_fail(e, "cudaMalloc(L2 flush buffer)");
+        }
+    }
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "preparing tuning inputs");
+    }
+    TimeOpts to;
+    to.repeats = o.repeats;
+    to.warmup = o.warmup;
+    to.flush_l2 = o.flush_l2;
+    to.graph_below_ms = o.graph_below_us < 0 ? -1.0 : o.graph_below_us * 1e-3;
+    int threads = o.compile_threads > 0 ? o.compile_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+    auto* t = new ct_table();
+    {
+        CompilePool pool(threads, o.cache_dir ? std::string(o.cache_dir) : cache_dir_setting());
+        GpuEvaluator ev(*p, to, img, h_filter, out, pool, flush, flush_bytes, stream);
+        rc = run_strategy(*p, s->s, st, o, valid, ev, *t, 2 * threads + 4);
+        if (rc == CT_OK && ev.fatal != CT_OK) rc = ev.fatal;
+        if (rc == CT_OK && ev.best()) put_variant(ev.best());
+    }
+    cleanup();
+    if (rc != CT_OK) {
+        delete t;
+        return rc;
+    }
+    t->info.wall_ms = now_ms() - t0;
+    if (best_out && t->info.best_row >= 0) *best_out = t->rows[(size_t)t->info.best_row].cfg;
+    *table_out = t;
+    if (t->info.best_row < 0) return fail(CT_ERR_LAUNCH, "every evaluated configuration failed");
+    return CT_OK;
+}
+
+}  // namespace ct

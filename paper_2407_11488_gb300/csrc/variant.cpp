@@ -1,0 +1,385 @@
+// Variant builder: NVRTC compile of the correlation template to an sm_103a
+// cubin, on-disk and in-memory caches, module loading and the launch.
+#include "ct_internal.hpp"
+
+#include <nvrtc.h>
+
+#include <cerrno>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <sys/stat.h>
+#include <unistd.h>
+
+namespace ct {
+
+// The kernel template source, embedded at build time.
+static const char kCorr2dSource[] =
+#include "corr2d_src.inc"
+    ;
+
+static const char* kArch = "--gpu-architecture=sm_103a";
+
+uint64_t VariantKey::packed() const
+{
+    uint64_t k = 0;
+    k = k * 2048 + (uint64_t)cfg.block_x;
+    k = k * 2048 + (uint64_t)cfg.block_y;
+    k = k * 32 + (uint64_t)cfg.tile_x;
+    k = k * 32 + (uint64_t)cfg.tile_y;
+    k = k * 2 + (uint64_t)cfg.use_smem;
+    k = k * 2 + (uint64_t)cfg.unroll;
+    k = k * 64 + (uint64_t)fw;
+    k = k * 64 + (uint64_t)fh;
+    k = k * 4 + (uint64_t)dtype;
+    return k;
+}
+
+std::string VariantKey::describe() const
+{
+    char b[160];
+    snprintf(b, sizeof b, "bx=%d by=%d tx=%d ty=%d smem=%d unroll=%d fw=%d fh=%d dtype=%d", cfg.block_x,
+             cfg.block_y, cfg.tile_x, cfg.tile_y, cfg.use_smem, cfg.unroll, fw, fh, dtype);
+    return b;
+}
+
+Variant::~Variant()
+{
+    if (lib) cudaLibraryUnload(lib);
+}
+
+static std::vector<std::string> nvrtc_options(const VariantKey& k)
+{
+    std::vector<std::string> o = {kArch, "--std=c++17", "--ptxas-options=-v", "-lineinfo"};
+    auto def = [&](const char* n, int v) { o.push_back(std::string("-D") + n + "=" + std::to_string(v)); };
+    def("CT_BX", k.cfg.block_x);
+    def("CT_BY", k.cfg.block_y);
+    def("CT_TX", k.cfg.tile_x);
+    def("CT_TY", k.cfg.tile_y);
+    def("CT_SMEM", k.cfg.use_smem);
+    def("CT_UNROLL", k.cfg.unroll);
+    def("CT_FW", k.fw);
+    def("CT_FH", k.fh);
+    def("CT_DTYPE", k.dtype);
+    // Extra NVRTC options from the environment (space separated), e.g. to
+    // inject a compile failure when testing how failures are recorded.
+    if (const char* extra = getenv("CONVTUNE_NVRTC_EXTRA")) {
+        std::istringstream is(extra);
+        std::string tok;
+        while (is >> tok) o.push_back(tok);
+    }
+    return o;
+}
+
+static uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull)
+{
+    const unsigned char* p = (const unsigned char*)data;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+static uint64_t cache_hash(const std::vector<std::string>& opts)
+{
+    int maj = 0, min = 0;
+    nvrtcVersion(&maj, &min);
+    uint64_t h = fnv1a(kCorr2dSource, sizeof kCorr2dSource);
+    for (const auto& s : opts) h = fnv1a(s.c_str(), s.size() + 1, h);
+    int v[2] = {maj, min};
+    return fnv1a(v, sizeof v, h);
+}
+
+static void parse_ptxas(Variant& v)
+{
+    v.regs = 0;
+    v.spill_bytes = 0;
+    const char* p = strstr(v.log.c_str(), "Used ");
+    if (p) v.regs = atoi(p + 5);
+    const char* s = strstr(v.log.c_str(), "bytes spill stores");
+    if (s) {
+        const char* b = s;
+        while (b > v.log.c_str() && (b[-1] == ' ' || (b[-1] >= '0' && b[-1] <= '9'))) --b;
+        v.spill_bytes += atoi(b);
+        const char* l = strstr(s, ", ");
+        if (l) v.spill_bytes += atoi(l + 2);
+    }
+}
+
+static bool read_file(const std::string& path, std::string& out)
+{
+    std::ifstream f(path, std::ios::binary);
+    if (!f) return false;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    out = ss.str();
+    return true;
+}
+
+static void write_file_atomic(const std::string& path, const void* data, size_t n)
+{
+    std::string tmp = path + ".tmp" + std::to_string((long long)getpid()) + "_" +
+                      std::to_string((unsigned long long)std::hash<std::thread::id>{}(std::this_thread::get_id()));
+    FILE* f = fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    bool ok = fwrite(data, 1, n, f) == n;
+    ok = (fclose(f) == 0) && ok;
+    if (ok) rename(tmp.c_str(), path.c_str());
+    else unlink(tmp.c_str());
+}
+
+static void mkdirs(const std::string& dir)
+{
+    std::string cur;
+    for (size_t i = 0; i <= dir.size(); ++i) {
+        if (i == dir.size() || dir[i] == '/') {
+            if (!cur.empty()) mkdir(cur.c_str(), 0775);
+        }
+        if (i < dir.size()) cur.push_back(dir[i]);
+    }
+}
+
+VariantPtr compile_variant(const VariantKey& k, const std::string& cache_dir)
+{
+    auto v = std::make_shared<Variant>();
+    v->key = k;
+    ct_problem p{};
+    p.filter_w = k.fw;
+    p.filter_h = k.fh;
+    v->smem = smem_bytes(p, k.cfg);
+    const std::vector<std::string> opts = nvrtc_options(k);
+    std::string base;
+    if (!cache_dir.empty()) {
+        char hex[32];
+        snprintf(hex, sizeof hex, "%016llx", (unsigned long long)cache_hash(opts));
+        base = cache_dir + "/ct-" + hex;
+        std::string bin, log;
+        if (read_file(base + ".cubin", bin) && read_file(base + ".log", log) && !bin.empty()) {
+            v->cubin.assign(bin.begin(), bin.end());
+            v->log = log;
+            parse_ptxas(*v);
+            v->from_cache = true;
+            return v;
+        }
+    }
+    const double t0 = now_ms();
+    nvrtcProgram prog = nullptr;
+    nvrtcResult r = nvrtcCreateProgram(&prog, kCorr2dSource, "corr2d.cu", 0, nullptr, nullptr);
+    if (r != NVRTC_SUCCESS) {
+        v->status = CT_ERR_COMPILE;
+        v->error = std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(r);
+        return v;
+    }
+    std::vector<const char*> co;
+    for (const auto& s : opts) co.push_back(s.c_str());
+    r = nvrtcCompileProgram(prog, (int)co.size(), co.data());
+    size_t ls = 0;
+    nvrtcGetProgramLogSize(prog, &ls);
+    std::string log(ls, '\0');
+    if (ls) nvrtcGetProgramLog(prog, &log[0]);
+    while (!log.empty() && log.back() == '\0') log.pop_back();
+    v->log = log;
+    if (r != NVRTC_SUCCESS) {
+        v->status = CT_ERR_COMPILE;
+        v->error = std::string("NVRTC failed for ") + k.describe() + ": " + nvrtcGetErrorString(r) + "\n" + log;
+        nvrtcDestroyProgram(&prog);
+        return v;
+    }
+    size_t cs = 0;
+    nvrtcGetCUBINSize(prog, &cs);
+    v->cubin.resize(cs);
+    if (cs) nvrtcGetCUBIN(prog, v->cubin.data());
+    nvrtcDestroyProgram(&prog);
+    v->compile_ms = now_ms() - t0;
+    parse_ptxas(*v);
+    if (!base.empty()) {
+        mkdirs(cache_dir);
+        write_file_atomic(base + ".log", v->log.data(), v->log.size());
+        write_file_atomic(base + ".cubin", v->cubin.data(), v->cubin.size());
+    }
+    return v;
+}
+
+// ------------------------------------------------------- in-memory cache ---
+static std::mutex g_cache_mu;
+static std::unordered_map<uint64_t, VariantPtr>& cache_map()
+{
+    static auto* m = new std::unordered_map<uint64_t, VariantPtr>();
+    return *m;
+}
+static std::unordered_map<uint64_t, std::shared_future<VariantPtr>>& pending_map()
+{
+    static auto* m = new std::unordered_map<uint64_t, std::shared_future<VariantPtr>>();
+    return *m;
+}
+
+std::string& cache_dir_setting()
+{
+    static std::string* dir = [] {
+        const char* e = getenv("CONVTUNE_CACHE_DIR");
+        return new std::string(e ? e : "");
+    }();
+    return *dir;
+}
+
+VariantPtr get_variant(const VariantKey& k)
+{
+    const uint64_t key = k.packed();
+    std::shared_ptr<std::promise<VariantPtr>> mine;
+    std::shared_future<VariantPtr> fut;
+    std::string dir;
+    {
+        std::lock_guard<std::mutex> g(g_cache_mu);
+        auto it = cache_map().find(key);
+        if (it != cache_map().end()) return it->second;
+        auto pit = pending_map().find(key);
+        if (pit != pending_map().end()) {
+            fut = pit->second;
+        } else {
+            mine = std::make_shared<std::promise<VariantPtr>>();
+            fut = mine->get_future().share();
+            pending_map()[key] = fut;
+            dir = cache_dir_setting();
+        }
+    }
+    if (mine) {
+        VariantPtr v = compile_variant(k, dir);
+        {
+            std::lock_guard<std::mutex> g(g_cache_mu);
+            if (v->status == CT_OK) cache_map()[key] = v;
+            pending_map().erase(key);
+        }
+        mine->set_value(v);
+        return v;
+    }
+    return fut.get();
+}
+
+void put_variant(const VariantPtr& v)
+{
+    if (!v || v->status != CT_OK) return;
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    cache_map()[v->key.packed()] = v;
+}
+
+void clear_variants()
+{
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    cache_map().clear();
+}
+
+// ------------------------------------------------------------- loading ----
+ct_status require_device()
+{
+    int dev = -1, n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return fail(CT_ERR_UNSUPPORTED, "no CUDA device is available (%s)",
+                    e == cudaSuccess ? "0 devices" : cudaGetErrorString(e));
+    }
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    int maj = 0, min = 0;
+    cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&min, cudaDevAttrComputeCapabilityMinor, dev);
+    if (maj != 10 || min != 3)
+        return fail(CT_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library targets sm_103a (GB300) only", dev,
+                    maj, min);
+    return CT_OK;
+}
+
+ct_status load_variant(Variant& v)
+{
+    if (v.status != CT_OK) return fail((ct_status)v.status, "%s", v.error.c_str());
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> g(v.mu);
+    if (!v.lib) {
+        e = cudaLibraryLoadData(&v.lib, v.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+        if (e != cudaSuccess) {
+            v.lib = nullptr;
+            return cuda_fail(e, "cudaLibraryLoadData");
+        }
+        e = cudaLibraryGetKernel(&v.kern, v.lib, "ct_corr2d");
+        if (e != cudaSuccess) return cuda_fail(e, "cudaLibraryGetKernel");
+    }
+    if (v.loaded_device != dev || v.smem_attr != v.smem) {
+        e = cudaFuncSetAttribute((const void*)v.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
+        v.loaded_device = dev;
+        v.smem_attr = v.smem;
+    }
+    return CT_OK;
+}
+
+void unload_variant(Variant& v)
+{
+    std::lock_guard<std::mutex> g(v.mu);
+    if (v.lib) cudaLibraryUnload(v.lib);
+    v.lib = nullptr;
+    v.kern = nullptr;
+    v.loaded_device = -1;
+    v.smem_attr = -1;
+}
+
+// -------------------------------------------------------------- launch ----
+ct_status check_buffers(const ct_problem& p, const void* d_image, const void* h_filter, const float* d_out)
+{
+    if (!h_filter) return fail(CT_ERR_INVALID_ARG, "filter pointer is NULL");
+    if (p.out_w == 0 || p.out_h == 0) return CT_OK;
+    if (!d_image || !d_out) return fail(CT_ERR_INVALID_ARG, "image or output pointer is NULL");
+    if (((uintptr_t)d_image & 15) || ((uintptr_t)d_out & 15))
+        return fail(CT_ERR_INVALID_ARG, "image and output must be 16-byte aligned");
+    return CT_OK;
+}
+
+// Parameter block of ct_corr2d, laid out as the device struct CtParams:
+// in, out, in_pitch, out_pitch (8 bytes each), out_w, out_h, in_w, in_h
+// (4 bytes each), then filter_h*filter_w floats.
+static constexpr size_t kParamHeader = 48;
+
+ct_status launch_variant(Variant& v, const ct_problem& p, const void* d_image, const void* h_filter,
+                         float* d_out, cudaStream_t stream)
+{
+    if (p.out_w == 0 || p.out_h == 0) return CT_OK;
+    ct_status s = load_variant(v);
+    if (s != CT_OK) return s;
+    const ct_config& c = v.key.cfg;
+    const int64_t tw = (int64_t)c.block_x * c.tile_x, th = (int64_t)c.block_y * c.tile_y;
+    const int64_t gx = (p.out_w + tw - 1) / tw, gy = (p.out_h + th - 1) / th;
+    if (gx > 0x7fffffffLL || gy > 65535)
+        return fail(CT_ERR_INVALID_ARG, "grid %lldx%lld exceeds the launch limits for this config", (long long)gx,
+                    (long long)gy);
+    const int nt = p.filter_w * p.filter_h;
+    alignas(16) unsigned char buf[kParamHeader + 4 * CT_MAX_FILTER * CT_MAX_FILTER];
+    const void* in_ptr = d_image;
+    void* out_ptr = d_out;
+    const int64_t ipitch = p.in_pitch, opitch = p.out_pitch;
+    const int32_t dims[4] = {p.out_w, p.out_h, (int32_t)in_w(p), (int32_t)in_h(p)};
+    memcpy(buf + 0, &in_ptr, 8);
+    memcpy(buf + 8, &out_ptr, 8);
+    memcpy(buf + 16, &ipitch, 8);
+    memcpy(buf + 24, &opitch, 8);
+    memcpy(buf + 32, dims, 16);
+    float* taps = reinterpret_cast<float*>(buf + kParamHeader);
+    if (p.dtype == CT_F32) {
+        memcpy(taps, h_filter, 4 * (size_t)nt);
+    } else {
+        const uint16_t* hb = (const uint16_t*)h_filter;
+        for (int i = 0; i < nt; ++i) {
+            uint32_t u = (uint32_t)hb[i] << 16;
+            memcpy(&taps[i], &u, 4);
+        }
+    }
+    void* args[1] = {buf};
+    cudaError_t e = cudaLaunchKernel((const void*)v.kern, dim3((unsigned)gx, (unsigned)gy, 1),
+                                     dim3((unsigned)c.block_x, (unsigned)c.block_y, 1), args, (size_t)v.smem, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchKernel(ct_corr2d)");
+    return CT_OK;
+}
+
+}  // namespace ct
