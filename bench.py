@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--seed", type=int, default=0, help="strategy seed")
     ap.add_argument("--cache-dir", default=None)
     ap.add_argument("--table-out", default=None, help="write the tuning table (JSONL)")
+    ap.add_argument("--config", default=None,
+                    help="bx,by,tx,ty,smem,unroll: skip tuning and time this configuration")
+    ap.add_argument("--cold-cache", action="store_true",
+                    help="give every strategy its own empty cubin cache (cold compile timings)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -261,19 +265,30 @@ def run_ours(args):
 
     # ---- tuning (before the timed region)
     tuning = {}
-    tab = ct.tune(p, space, args.strategy, image=d_img, filt=f, out=d_out, seed=args.seed,
-                  write_path=args.table_out)
-    best = tab.best
-    tuning[args.strategy] = tab.info
-    for extra in [s for s in args.extra_strategies.split(",") if s and s != args.strategy]:
-        tuning[extra] = ct.tune(p, space, extra, image=d_img, filt=f, out=d_out, seed=args.seed).info
-    valid = tab.valid()
-    t_sorted = sorted(r["t_med_ms"] for r in valid)
-    t_best = t_sorted[0]
-    t_med = statistics.median(t_sorted)
-    perf = sorted(flops / (r["t_med_ms"] * 1e-3) for r in valid)
-    impact = max(perf) / statistics.median(perf)
-    frac10 = sum(1 for t in t_sorted if t <= 1.10 * t_best) / len(t_sorted)
+    analysis = {}
+    if args.config:
+        best = ct.config(*[int(v) for v in args.config.split(",")])
+        n_valid = ct.Space(space).count(p)[1]
+    else:
+        strategies = [args.strategy] + [s for s in args.extra_strategies.split(",") if s and s != args.strategy]
+        tab = None
+        for k, strat in enumerate(strategies):
+            cdir = tempfile.mkdtemp(prefix=f"convtune-{strat}-") if args.cold_cache else None
+            t = ct.tune(p, space, strat, image=d_img, filt=f, out=d_out, seed=args.seed, cache_dir=cdir,
+                        write_path=args.table_out if k == 0 else None)
+            tuning[strat] = dict(t.info, best=t.best.as_dict(),
+                                 best_ms=t.rows[t.info["best_row"]]["t_med_ms"])
+            if k == 0:
+                tab = t
+        best = tab.best
+        n_valid = tab.info["n_valid_space"]
+        valid = tab.valid()
+        t_sorted = sorted(r["t_med_ms"] for r in valid)
+        perf = sorted(flops / (r["t_med_ms"] * 1e-3) for r in valid)
+        analysis = {"tuned_vs_median": statistics.median(t_sorted) / t_sorted[0],
+                    "frac_within_10pct": sum(1 for t in t_sorted if t <= 1.10 * t_sorted[0]) / len(t_sorted),
+                    "impact": max(perf) / statistics.median(perf),
+                    "analysis_over": f"{len(valid)} configs measured by {args.strategy}"}
 
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(int(2 * max(info.l2_bytes, 64 << 20)), dtype=torch.uint8, device=dev)
@@ -302,11 +317,11 @@ def run_ours(args):
         ms = [a.elapsed_time(b) for a, b in ev]
         return ms, t_wall, t_wall_end
 
-    default = ct.default_config()
-    ms_def, _, _ = timed_loop(default, max(50, args.steps // 10), 5)
     clocks.mark("timed_start")
     ms, tw0, tw1 = timed_loop(best, args.steps, max(3, args.warmup))
     clocks.mark("timed_end")
+    default = ct.default_config()
+    ms_def, _, _ = timed_loop(default, max(50, args.steps // 10), 5)
     t_step = sum(ms) / len(ms)
     if world > 1:
         t = torch.tensor([t_step], device=dev)
@@ -346,19 +361,19 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"corr2d out {ow}x{oh}, filter {fs}x{fs}, uniform[-1,1) seed {seed}",
-                   "space": f"{space} ({tab.info['n_valid_space']} valid configs)",
-                   "strategy": args.strategy, "tuned_config": best.as_dict(),
+                   "space": f"{space} ({n_valid} valid configs)",
+                   "strategy": "fixed --config" if args.config else args.strategy,
+                   "tuned_config": best.as_dict(),
                    "l2": "flushed (2x L2 write) between timed iterations", "parallelism": f"replicas x{world}"},
         "pct_fp32_peak": 100.0 * achieved / fp32_peak,
         "tuned_vs_default": statistics.median(ms_def) / statistics.median(ms),
         "default_ms": statistics.median(ms_def),
-        "tuned_vs_median": t_med / t_best,
-        "frac_within_10pct": frac10,
-        "impact": impact,
-        "analysis_over": f"{len(valid)} configs measured by {args.strategy}",
+        **analysis,
         "tuning": {k: {"wall_s": v["wall_ms"] / 1e3, "compile_wait_s": v["compile_wall_ms"] / 1e3,
                        "compile_cpu_s": v["compile_cpu_ms"] / 1e3, "bench_s": v["bench_ms"] / 1e3,
-                       "evals": v["n_rows"], "space_valid": v["n_valid_space"]} for k, v in tuning.items()},
+                       "evals": v["n_rows"], "space_valid": v["n_valid_space"], "best": v["best"],
+                       "best_ms": v["best_ms"], "cold_cache": bool(args.cold_cache)}
+                   for k, v in tuning.items()},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": int(img.nbytes),
                 "d2h_bytes_per_step": int(h_out.numel() * 4), "ms_per_step": te * 1e3},
