@@ -157,9 +157,13 @@ CT_API ct_status ct_conv2d(const ct_problem* p, const ct_config* c, const void* 
 
 /* End-to-end form of ct_conv2d for host-resident data: copies h_image to
  * d_image_ws, runs the correlation into d_out_ws and copies the result to
- * h_out, all on stream, then synchronises the stream.  The workspaces are
- * caller-owned device buffers of the sizes ct_conv2d needs; h_image and
- * h_out should be pinned for the copies to run at full speed. */
+ * h_out, then synchronises `stream`.  The work is split into bands of output
+ * rows (up to 8, at least 256 rows each) on library-owned streams so that the
+ * copy-in of one band, the correlation of the previous one and the copy-out
+ * of the one before overlap; it starts after the work already queued on
+ * `stream`.  The workspaces are caller-owned device buffers of the sizes
+ * ct_conv2d needs; h_image and h_out should be pinned host memory.  Calls on
+ * one device are serialised by the library. */
 CT_API ct_status ct_conv2d_host(const ct_problem* p, const ct_config* c, const void* h_image,
                                 const void* h_filter, float* h_out, void* d_image_ws,
                                 float* d_out_ws, void* stream);

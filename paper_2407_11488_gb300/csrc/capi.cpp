@@ -1,6 +1,7 @@
 // The C-ABI of libconvtune.so (declared in include/convtune.h).
 #include "ct_internal.hpp"
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 
@@ -103,6 +104,26 @@ CT_API ct_status ct_conv2d(const ct_problem* p, const ct_config* c, const void* 
     return launch_variant(*v, *p, d_image, h_filter, d_out, (cudaStream_t)stream);
 }
 
+// Streams and events of the host-buffer pipeline, one set per device.
+struct HostPipe {
+    std::mutex mu;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr, comp[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> ev;
+    bool ready = false;
+};
+
+static HostPipe& host_pipe(int dev)
+{
+    static std::mutex m;
+    static auto* pipes = new std::unordered_map<int, HostPipe*>();
+    std::lock_guard<std::mutex> g(m);
+    HostPipe*& hp = (*pipes)[dev];
+    if (!hp) hp = new HostPipe();
+    return *hp;
+}
+
+static constexpr int kMaxBands = 8;
+
 CT_API ct_status ct_conv2d_host(const ct_problem* p, const ct_config* c, const void* h_image, const void* h_filter,
                                 float* h_out, void* d_image_ws, float* d_out_ws, void* stream)
 {
@@ -116,15 +137,62 @@ CT_API ct_status ct_conv2d_host(const ct_problem* p, const ct_config* c, const v
     if ((s = check_config(*p, *c, 0)) != CT_OK) return s;
     VariantPtr v = get_variant(VariantKey{*c, p->filter_w, p->filter_h, p->dtype});
     if (v->status != CT_OK) return fail((ct_status)v->status, "%s", v->error.c_str());
-    cudaStream_t st = (cudaStream_t)stream;
-    const size_t in_bytes = (size_t)(in_h(*p) * p->in_pitch * elem_size(p->dtype));
-    const size_t out_bytes = (size_t)(p->out_h * p->out_pitch * 4);
-    cudaError_t e = cudaMemcpyAsync(d_image_ws, h_image, in_bytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(H2D image)");
-    if ((s = launch_variant(*v, *p, d_image_ws, h_filter, d_out_ws, st)) != CT_OK) return s;
-    if ((e = cudaMemcpyAsync(h_out, d_out_ws, out_bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-        return cuda_fail(e, "cudaMemcpyAsync(D2H output)");
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    HostPipe& hp = host_pipe(dev);
+    std::lock_guard<std::mutex> g(hp.mu);
+    if (!hp.ready) {
+        cudaStream_t* all[4] = {&hp.copy_in, &hp.copy_out, &hp.comp[0], &hp.comp[1]};
+        for (auto* st : all)
+            if ((e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamCreate(host pipeline)");
+        hp.ev.resize(2 + 2 * kMaxBands);
+        for (auto& ev : hp.ev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "cudaEventCreate(host pipeline)");
+        hp.ready = true;
+    }
+    // Bands of output rows: band b copies in the input rows it needs that no
+    // earlier band copied, runs on alternating compute streams, and copies
+    // its output rows back; consecutive bands overlap copy-in, compute and
+    // copy-out.
+    const int64_t es = elem_size(p->dtype);
+    const int bands = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxBands, p->out_h / 256));
+    cudaStream_t user = (cudaStream_t)stream;
+    cudaEvent_t start = hp.ev[0], done = hp.ev[1];
+    cudaEventRecord(start, user);
+    cudaStreamWaitEvent(hp.copy_in, start, 0);
+    int64_t copied_rows = 0;
+    for (int b = 0; b < bands; ++b) {
+        const int64_t y0 = (int64_t)p->out_h * b / bands, y1 = (int64_t)p->out_h * (b + 1) / bands;
+        const int64_t need = std::min<int64_t>(in_h(*p), y1 + p->filter_h - 1);
+        cudaEvent_t e_in = hp.ev[2 + 2 * b], e_comp = hp.ev[3 + 2 * b];
+        if (need > copied_rows) {
+            const size_t off = (size_t)(copied_rows * p->in_pitch * es);
+            e = cudaMemcpyAsync((char*)d_image_ws + off, (const char*)h_image + off,
+                                (size_t)((need - copied_rows) * p->in_pitch * es), cudaMemcpyHostToDevice,
+                                hp.copy_in);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(H2D image band)");
+            copied_rows = need;
+        }
+        cudaEventRecord(e_in, hp.copy_in);
+        cudaStream_t cs = hp.comp[b & 1];
+        cudaStreamWaitEvent(cs, e_in, 0);
+        ct_problem pb = *p;
+        pb.out_h = (int32_t)(y1 - y0);
+        if ((s = launch_variant(*v, pb, (const char*)d_image_ws + y0 * p->in_pitch * es, h_filter,
+                                d_out_ws + y0 * p->out_pitch, cs)) != CT_OK)
+            return s;
+        cudaEventRecord(e_comp, cs);
+        cudaStreamWaitEvent(hp.copy_out, e_comp, 0);
+        e = cudaMemcpyAsync(h_out + y0 * p->out_pitch, d_out_ws + y0 * p->out_pitch,
+                            (size_t)((y1 - y0) * p->out_pitch * 4), cudaMemcpyDeviceToHost, hp.copy_out);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(D2H output band)");
+    }
+    cudaEventRecord(done, hp.copy_out);
+    cudaStreamWaitEvent(user, done, 0);
+    if ((e = cudaStreamSynchronize(user)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return CT_OK;
 }
 

@@ -230,3 +230,21 @@ def test_tune_strategies_on_gpu(ctlib, cuda_device, strategy):
     assert tab.best.as_tuple() == best["cfg"].as_tuple()
     info = tab.info
     assert info["wall_ms"] >= info["bench_ms"] > 0 and info["compile_cpu_ms"] >= 0
+
+
+def test_host_entry_point_bands(ctlib, cuda_device):
+    """The banded host pipeline (8 bands here) gives the device path's bits."""
+    ow, oh, fw, fh = 1000, 2048 + 37, 9, 13
+    img, f = synthetic.make_problem(12, ow, oh, fw, fh)
+    d_img = upload_image(img, cuda_device)
+    c = ctlib.config(32, 8, 4, 5, 1, 0)
+    out, ok = run_config(ctlib, d_img, f, c, ow, oh, in_w=ow + fw - 1)
+    assert ok
+    p = ctlib.problem_for(d_img, f, in_w=ow + fw - 1)
+    h_img = torch.from_numpy(img).pin_memory()
+    h_out = torch.full((oh, p.out_pitch), float("nan"), dtype=torch.float32).pin_memory()
+    ws_img = torch.zeros_like(d_img)
+    ws_out = torch.zeros((oh, p.out_pitch), dtype=torch.float32, device=cuda_device)
+    for _ in range(2):
+        ctlib.conv2d_host(p, c, h_img, np.ascontiguousarray(f), h_out, ws_img, ws_out)
+        assert np.array_equal(h_out.numpy()[:, :ow].view(np.uint32), out.view(np.uint32))
