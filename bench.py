@@ -40,6 +40,7 @@ WORKLOADS = {
     "full": (4096, 4096, 17, 1, "full"),
     "small": (256, 256, 5, 0, "small"),
 }
+BATCH = {"count": 64, "side_lo": 128, "side_hi": 4096, "filters": (3, 5, 7, 11, 17), "seed": 2}
 FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM per clock (4 partitions x 32)
 
 
@@ -49,8 +50,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOADS), default="full")
-    ap.add_argument("--strategy", choices=["random", "anneal", "brute"], default="random")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch"], default="full")
+    ap.add_argument("--anneal-chains", type=int, default=4)
+    ap.add_argument("--batch-plain-evals", type=int, default=120,
+                    help="annealing budget per filter size for the per-problem path of the batch workload")
+    ap.add_argument("--strategy", choices=["random", "anneal", "brute"], default="anneal")
     ap.add_argument("--extra-strategies", default="", help="comma list also run (wall time reported)")
     ap.add_argument("--seed", type=int, default=0, help="strategy seed")
     ap.add_argument("--cache-dir", default=None)
@@ -168,7 +172,7 @@ def run_reference(args):
     import oracle
     import synthetic
     oracle.build()
-    ow, oh, fs, seed, _ = WORKLOADS[args.workload]
+    ow, oh, fs, seed, _ = WORKLOADS.get(args.workload, WORKLOADS["full"])
     img, f = synthetic.make_problem(seed, ow, oh, fs, fs)
     steps = args.steps + args.warmup
     dt = cpu_rate_sample(img, f, ow, 8) / 8.0            # seconds per output row
@@ -275,7 +279,7 @@ def run_ours(args):
         for k, strat in enumerate(strategies):
             cdir = tempfile.mkdtemp(prefix=f"convtune-{strat}-") if args.cold_cache else None
             t = ct.tune(p, space, strat, image=d_img, filt=f, out=d_out, seed=args.seed, cache_dir=cdir,
-                        write_path=args.table_out if k == 0 else None)
+                        write_path=args.table_out if k == 0 else None, anneal_chains=args.anneal_chains)
             tuning[strat] = dict(t.info, best=t.best.as_dict(),
                                  best_ms=t.rows[t.info["best_row"]]["t_med_ms"])
             if k == 0:
@@ -393,10 +397,170 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """64 uneven correlations: the plain per-problem path (one ct_conv2d per
+    problem with the configuration tuned for its filter size) against one
+    persistent launch of the batched kernel (graph), same inputs and outputs."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2407_11488_gb300 import build as _build
+    if local == 0:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    import paper_2407_11488_gb300 as ct
+    import synthetic
+
+    ct.set_cache_dir(args.cache_dir or os.path.join(tempfile.gettempdir(), f"convtune-cache-{os.getuid()}"))
+    info = ct.device_query()
+    pk = peaks()
+    sm_max_mhz = float(pk.get("sm_max_mhz") or (info.clock_max_khz / 1e3) or 2070.0)
+    fp32_peak = info.sm_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    shapes = synthetic.uneven_batch(BATCH["seed"], BATCH["count"], BATCH["side_lo"], BATCH["side_hi"],
+                                    BATCH["filters"])
+    probs = []
+    for k, (side, fs) in enumerate(shapes):
+        img, f = synthetic.make_problem(BATCH["seed"] * 100000 + k, side, side, fs, fs)
+        d_img = torch.from_numpy(img).to(dev)
+        out = torch.empty((side, synthetic.round_up(side, 4)), dtype=torch.float32, device=dev)
+        probs.append((img, np.ascontiguousarray(f), d_img, out, side, fs))
+    flops = sum(2.0 * side * side * fs * fs for side, fs in shapes)
+
+    # plain path: tune once per filter size on that size's largest problem
+    t0 = time.time()
+    cfg_for = {}
+    tuning = {}
+    for fs in sorted(set(fs for _, fs in shapes)):
+        big = max((p for p in probs if p[5] == fs), key=lambda p: p[4])
+        _, f, d_img, out, side, _ = big
+        pr = ct.problem_for(d_img, f, in_w=side + fs - 1)
+        tab = ct.tune(pr, "full", "anneal", image=d_img, filt=f, out=out, seed=args.seed,
+                      max_evals=args.batch_plain_evals, anneal_chains=args.anneal_chains)
+        cfg_for[fs] = tab.best
+        tuning[f"plain_f{fs}"] = {"side": side, "best": tab.best.as_dict(), "wall_s": tab.info["wall_ms"] / 1e3,
+                                  "evals": tab.info["n_rows"]}
+    plain_tune_s = time.time() - t0
+    plain_args = []
+    for img, f, d_img, out, side, fs in probs:
+        pr = ct.problem_for(d_img, f, in_w=side + fs - 1)
+        pr.out_pitch = out.stride(0)
+        plain_args.append((pr, cfg_for[fs], d_img.data_ptr(), f, out.data_ptr()))
+
+    t0 = time.time()
+    batch = ct.Batch([(d_img, f, out, side + fs - 1) for (_, f, d_img, out, side, fs) in probs], tune=True,
+                     max_tune_items=6)
+    batch_plan_s = time.time() - t0
+    binfo = batch.info()
+
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(int(2 * max(info.l2_bytes, 64 << 20)), dtype=torch.uint8, device=dev)
+
+    def plain_step():
+        for pr, cfg, di, f, do in plain_args:
+            ct.conv2d_raw(pr, cfg, di, f, do, stream.cuda_stream)
+
+    def batch_step():
+        batch.run(stream)
+
+    def timed(step, k, w):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        with torch.cuda.stream(stream):
+            for _ in range(w):
+                step()
+            stream.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            for i in range(k):
+                flush.fill_(i & 0xFF)
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+            stream.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    k = max(5, min(args.steps, 200))
+    clocks = ClockSampler(local)
+    clocks.start()
+    tb0 = time.time()
+    ms_batch = timed(batch_step, k, max(3, args.warmup))
+    tb1 = time.time()
+    ms_plain = timed(plain_step, k, max(3, args.warmup))
+    clocks.stop()
+    # the batched outputs equal the per-problem outputs bit for bit
+    batch_step()
+    stream.synchronize()
+    snap = [out.clone() for (_, _, _, out, _, _) in probs]
+    plain_step()
+    stream.synchronize()
+    identical = all(torch.equal(a.view(torch.int32), out.view(torch.int32))
+                    for a, (_, _, _, out, _, _) in zip(snap, probs))
+
+    # end to end: pinned host images in, outputs out, every step
+    h_imgs = [torch.from_numpy(img).pin_memory() for (img, *_rest) in probs]
+    h_outs = [torch.empty_like(out, device="cpu").pin_memory() for (_, _, _, out, _, _) in probs]
+    e_steps = max(3, min(k, 50))
+    with torch.cuda.stream(stream):
+        te0 = time.perf_counter()
+        for _ in range(e_steps):
+            for hi, (_, _, d_img, _, _, _) in zip(h_imgs, probs):
+                d_img.copy_(hi, non_blocking=True)
+            batch.run(stream)
+            for ho, (_, _, _, out, _, _) in zip(h_outs, probs):
+                ho.copy_(out, non_blocking=True)
+            stream.synchronize()
+        te = (time.perf_counter() - te0) / e_steps
+    t_b = statistics.mean(ms_batch)
+    t_p = statistics.mean(ms_plain)
+    q = sorted(ms_batch)
+    p99 = q[min(len(q) - 1, int(math.ceil(0.99 * len(q))) - 1)]
+    achieved = flops / (t_b * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": world * flops / (t_b * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": world,
+        "steps": k, "warmup": args.warmup, "ms_per_step": t_b, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{BATCH['count']} uneven FP32 correlations, square sides log-uniform in "
+                               f"[{BATCH['side_lo']},{BATCH['side_hi']}], filters {list(BATCH['filters'])}, "
+                               f"seed {BATCH['seed']}",
+                   "total_gflop": flops / 1e9, "l2": "flushed between timed iterations",
+                   "parallelism": f"replicas x{world}"},
+        "batched_p50_ms": statistics.median(ms_batch), "batched_p99_ms": p99,
+        "plain_gflops": world * flops / (t_p * 1e-3) / 1e9, "plain_ms_per_step": t_p,
+        "batched_vs_plain": t_p / t_b, "bit_identical_to_plain": identical,
+        "batch": {"buckets": batch.buckets(), **binfo, "plan_s": batch_plan_s},
+        "plain_tuning": {"wall_s": plain_tune_s, **tuning},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_basis": f"{info.sm_count} SMs x {FP32_LANES_PER_SM} x 2 x {sm_max_mhz:.0f} MHz"},
+        "e2e": {"value": world * flops / te / 1e9, "unit": "GFLOP/s",
+                "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in h_imgs)),
+                "d2h_bytes_per_step": int(sum(h.numel() * 4 for h in h_outs)), "ms_per_step": te * 1e3},
+        "gpu_launches": k,
+        "clocks": clocks.summary(tb0, tb1),
+        "device": info.name.decode(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -212,6 +212,9 @@ typedef struct {
     int32_t compile_threads;  /* 0: one per host core */
     int32_t graph_below_us;   /* kernels shorter than this are timed as a graph of
                                  back-to-back launches (0: 50 us; < 0: never) */
+    int32_t anneal_chains;    /* ANNEAL: walkers advanced in lock step, their
+                                 candidates compiled together (0: 1) */
+    int32_t reserved;
     const char* cache_dir;    /* cubin cache for this run (NULL: library setting) */
     const char* resume_path;  /* JSONL table: rows found there are not re-measured,
                                  new rows are appended (NULL: none) */
@@ -270,6 +273,73 @@ CT_API ct_status ct_table_info_get(const ct_table* t, ct_table_info* out);
 /* Writes the table as JSON lines (one object per row). */
 CT_API ct_status ct_table_write(const ct_table* t, const char* path);
 CT_API void ct_table_free(ct_table* t);
+
+
+/* ---- batched uneven problems (one persistent launch) ---------------------
+ *
+ * Many correlations of different image and filter sizes run in ONE launch of
+ * a persistent kernel, captured in a CUDA graph.  Problems are grouped into
+ * buckets (same filter size; image side below / at-or-above a split), each
+ * bucket gets its own compile-time tile routine, and every block of the launch
+ * takes (problem, tile) work items from a global counter until the list is
+ * empty.  Bucket tile shapes are chosen by measurement on the bucket's own
+ * problems; the default objective is the performance portability PP of Eq. 2
+ * over the bucket's shapes (harmonic mean of the per-shape efficiencies of
+ * Eq. 3), the alternative the bucket's summed time.  Results are bit-identical
+ * to ct_conv2d on each problem. */
+
+typedef struct {
+    const void* d_image;   /* in_h x in_pitch elements of the batch dtype (caller-owned, kept alive) */
+    float* d_out;          /* out_h x out_pitch floats (caller-owned, kept alive) */
+    const void* h_filter;  /* filter_h x filter_w host array (float or bf16 bits); copied at create */
+    int32_t out_w, out_h, filter_w, filter_h;
+    int64_t in_pitch, out_pitch;   /* elements; same alignment rules as ct_problem */
+} ct_batch_item;
+
+typedef struct {
+    int32_t block_x, block_y, tile_x, tile_y;
+} ct_bucket_config;
+
+typedef struct {
+    int32_t dtype;          /* ct_dtype of every image in the batch */
+    int32_t threads;        /* threads per block of the persistent kernel (0: 256) */
+    int32_t tune;           /* 1: choose each bucket's tile by measurement; 0: fixed default tiles */
+    int32_t objective;      /* 0: maximise PP over the bucket's shapes (Eq. 2); 1: minimise bucket time */
+    int32_t side_split;     /* image side splitting a filter size into two buckets (0: 512; < 0: no split) */
+    int32_t blocks_per_sm;  /* resident blocks per SM of the persistent grid (0: occupancy query) */
+    int32_t max_tune_items; /* problems per bucket measured while tuning (0: 12) */
+    int32_t reserved;
+} ct_batch_opts;
+
+typedef struct {
+    int32_t n_items, n_buckets;
+    int64_t n_work;         /* work items (tiles) per run */
+    int32_t grid, threads;
+    int32_t smem_bytes, regs;
+    double plan_ms, tune_ms, compile_cpu_ms;
+} ct_batch_info;
+
+typedef struct ct_batch ct_batch;
+
+/* Plans a batch: validates every item (as ct_conv2d would), buckets the
+ * problems, tunes (opts->tune) and compiles the persistent kernel, uploads the
+ * problem table, the filters and the work list, and captures the launch (work
+ * counter reset + kernel) in a CUDA graph.  Synchronous; device memory for the
+ * tables is owned by the plan.  Up to 16 buckets per batch. */
+CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct_batch_opts* opts,
+                                 ct_batch** out);
+/* Runs the planned batch once on `stream` (one graph launch; asynchronous).
+ * Runs of one plan must not overlap: they share its work counter. */
+CT_API ct_status ct_batch_run(ct_batch* b, void* stream);
+CT_API ct_status ct_batch_info_get(const ct_batch* b, ct_batch_info* out);
+/* Bucket k: its filter size, number of problems, tile configuration and the
+ * PP score (Eq. 2) of that configuration over the bucket's measured shapes
+ * (NaN when the bucket was not tuned). */
+CT_API ct_status ct_batch_bucket(const ct_batch* b, int32_t k, int32_t* filter_w, int32_t* filter_h,
+                                 int32_t* n_items, ct_bucket_config* cfg, double* pp);
+/* Bucket index of item i (in the order given to ct_batch_create). */
+CT_API int32_t ct_batch_item_bucket(const ct_batch* b, int32_t i);
+CT_API void ct_batch_free(ct_batch* b);
 
 #ifdef __cplusplus
 }

@@ -73,7 +73,7 @@ class DeviceInfo(ctypes.Structure):
 class TuneOpts(ctypes.Structure):
     _fields_ = [("seed", u64), ("sample_fraction", dbl), ("max_evals", i32), ("repeats", i32),
                 ("warmup", i32), ("flush_l2", i32), ("compile_threads", i32), ("graph_below_us", i32),
-                ("cache_dir", cp), ("resume_path", cp)]
+                ("anneal_chains", i32), ("reserved", i32), ("cache_dir", cp), ("resume_path", cp)]
 
 
 class Row(ctypes.Structure):
@@ -85,6 +85,25 @@ class Row(ctypes.Structure):
 class TableInfo(ctypes.Structure):
     _fields_ = [("strategy", i32), ("n_rows", i32), ("n_valid_space", i64), ("best_row", i64),
                 ("wall_ms", dbl), ("compile_wall_ms", dbl), ("compile_cpu_ms", dbl), ("bench_ms", dbl)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("d_image", vp), ("d_out", vp), ("h_filter", vp), ("out_w", i32), ("out_h", i32),
+                ("filter_w", i32), ("filter_h", i32), ("in_pitch", i64), ("out_pitch", i64)]
+
+
+class BucketConfig(ctypes.Structure):
+    _fields_ = [("block_x", i32), ("block_y", i32), ("tile_x", i32), ("tile_y", i32)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("dtype", i32), ("threads", i32), ("tune", i32), ("objective", i32), ("side_split", i32),
+                ("blocks_per_sm", i32), ("max_tune_items", i32), ("reserved", i32)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_items", i32), ("n_buckets", i32), ("n_work", i64), ("grid", i32), ("threads", i32),
+                ("smem_bytes", i32), ("regs", i32), ("plan_ms", dbl), ("tune_ms", dbl), ("compile_cpu_ms", dbl)]
 
 
 P = ctypes.POINTER
@@ -111,6 +130,12 @@ _SIGS = {
     "ct_table_info_get": (i32, [vp, P(TableInfo)]),
     "ct_table_write": (i32, [vp, cp]),
     "ct_table_free": (None, [vp]),
+    "ct_batch_create": (i32, [P(BatchItem), i32, P(BatchOpts), P(vp)]),
+    "ct_batch_run": (i32, [vp, vp]),
+    "ct_batch_info_get": (i32, [vp, P(BatchInfo)]),
+    "ct_batch_bucket": (i32, [vp, i32, P(i32), P(i32), P(i32), P(BucketConfig), P(dbl)]),
+    "ct_batch_item_bucket": (i32, [vp, i32]),
+    "ct_batch_free": (None, [vp]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -372,9 +397,9 @@ def _collect(t, best, write_path=None) -> Table:
 
 
 def _opts(seed=0, sample_fraction=0.0, max_evals=0, repeats=0, warmup=0, flush_l2=False, compile_threads=0,
-          graph_below_us=0, cache_dir=None, resume_path=None):
+          graph_below_us=0, anneal_chains=0, cache_dir=None, resume_path=None):
     return TuneOpts(seed, sample_fraction, max_evals, repeats, warmup, int(flush_l2), compile_threads,
-                    graph_below_us, cache_dir.encode() if cache_dir else None,
+                    graph_below_us, anneal_chains, 0, cache_dir.encode() if cache_dir else None,
                     resume_path.encode() if resume_path else None)
 
 
@@ -415,3 +440,65 @@ def tune_replay(problem: Problem, space, strategy, times_ms, **opts) -> Table:
         return _collect(t, best if st == CT_OK else None)
     _check(st)
     raise CTError(-5, "ct_tune_replay returned no table")
+
+
+# ------------------------------------------------------------------ batches ---
+class Batch:
+    """Many uneven correlations in one persistent launch (ct_batch_*).
+
+    ``problems`` is a list of (image, filt, out, in_w): CUDA image tensor
+    (in_h, in_pitch) with in_w valid columns, host filter (fh, fw), CUDA
+    float32 output tensor (out_h >= rows, out_pitch).  The tensors must stay
+    alive while the batch is used; filters are copied at creation."""
+
+    def __init__(self, problems, *, dtype=None, threads=256, tune=True, objective="pp", side_split=512,
+                 blocks_per_sm=0, max_tune_items=12):
+        import torch
+        self._keep = []
+        arr = (BatchItem * len(problems))()
+        dt = None
+        for k, (img, filt, out, in_w) in enumerate(problems):
+            p = problem_for(img, filt, in_w)
+            dt = p.dtype if dt is None else dt
+            if p.dtype != dt:
+                raise TypeError("all images of a batch share one dtype")
+            fb = _filter_bytes(filt, p.dtype)
+            if out.dtype != torch.float32 or not out.is_cuda:
+                raise TypeError("outputs must be CUDA float32 tensors")
+            self._keep += [img, out, fb]
+            arr[k] = BatchItem(img.data_ptr(), out.data_ptr(), fb.ctypes.data, p.out_w, p.out_h, p.filter_w,
+                               p.filter_h, p.in_pitch, out.stride(0))
+        o = BatchOpts(dt if dtype is None else dtype, threads, int(tune), 1 if objective == "time" else 0,
+                      side_split, blocks_per_sm, max_tune_items, 0)
+        h = vp()
+        _check(_load().ct_batch_create(arr, len(problems), ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h
+        self.n = len(problems)
+
+    def run(self, stream=None):
+        _check(_load().ct_batch_run(self.handle, _stream_ptr(stream)))
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        _check(_load().ct_batch_info_get(self.handle, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+
+    def buckets(self):
+        res = []
+        for k in range(self.info()["n_buckets"]):
+            fw, fh, n = i32(), i32(), i32()
+            c = BucketConfig()
+            pp = dbl()
+            _check(_load().ct_batch_bucket(self.handle, k, ctypes.byref(fw), ctypes.byref(fh), ctypes.byref(n),
+                                           ctypes.byref(c), ctypes.byref(pp)))
+            res.append({"filter": (fw.value, fh.value), "n_items": n.value, "pp": pp.value,
+                        "config": {f: getattr(c, f) for f, _ in BucketConfig._fields_}})
+        return res
+
+    def item_bucket(self, i: int) -> int:
+        return int(_load().ct_batch_item_bucket(self.handle, i))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ct_batch_free(self.handle)
+            self.handle = None

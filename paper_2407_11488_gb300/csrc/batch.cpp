@@ -1,0 +1,562 @@
+// Batched uneven correlations: bucketing, per-bucket tile tuning, work list,
+// the persistent launch and its CUDA graph.
+#include "ct_internal.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <numeric>
+
+namespace ct {
+
+static const char kBatchSource[] =
+#include "batch_src.inc"
+    ;
+
+namespace {
+
+struct TileCfg {
+    int bx = 32, tx = 4, ty = 4;
+};
+
+// Mirrors of the device structs in batch.cuh.
+struct DevProblem {
+    const void* in;
+    float* out;
+    int64_t in_pitch, out_pitch;
+    int32_t out_w, out_h, in_w, in_h;
+    int32_t bucket, tiles_x, filt_off, pad;
+};
+static_assert(sizeof(DevProblem) == 64, "DevProblem layout");
+struct DevParams {
+    const void* probs;
+    const void* work;
+    const float* filters;
+    unsigned* counter;
+    int32_t n_work;
+    int32_t pad;
+};
+static_assert(sizeof(DevParams) == 40, "DevParams layout");
+struct WorkItem {
+    uint32_t problem, tile;
+};
+
+struct BucketDesc {
+    int fw, fh;
+    TileCfg cfg;
+};
+
+int64_t tile_w(int threads, const TileCfg& c) { (void)threads; return (int64_t)c.bx * c.tx; }
+int64_t tile_h(int threads, const TileCfg& c) { return (int64_t)(threads / c.bx) * c.ty; }
+
+int64_t bucket_smem(int threads, const TileCfg& c, int fw, int fh)
+{
+    const int64_t hh = tile_h(threads, c) + fh - 1;
+    const int64_t sw = round_up(tile_w(threads, c) + fw - 1, 4);
+    return (fh * round_up(fw, 4) + hh * sw) * 4;
+}
+
+std::vector<std::string> batch_options(int threads, int dtype, const std::vector<BucketDesc>& b)
+{
+    std::vector<std::string> o = nvrtc_base_options();
+    auto def = [&](const std::string& n, int v) { o.push_back("-D" + n + "=" + std::to_string(v)); };
+    def("CT_NT", threads);
+    def("CT_DTYPE", dtype);
+    def("CT_NB", (int)b.size());
+    for (size_t k = 0; k < b.size(); ++k) {
+        const std::string p = "CT_B" + std::to_string(k) + "_";
+        def(p + "BX", b[k].cfg.bx);
+        def(p + "TX", b[k].cfg.tx);
+        def(p + "TY", b[k].cfg.ty);
+        def(p + "FW", b[k].fw);
+        def(p + "FH", b[k].fh);
+    }
+    add_env_options(o);
+    return o;
+}
+
+uint64_t options_key(const std::vector<std::string>& o)
+{
+    uint64_t h = 1469598103934665603ull ^ 0xB47C4ull;
+    for (const auto& s : o)
+        for (size_t i = 0; i <= s.size(); ++i) {
+            h ^= (unsigned char)(i < s.size() ? s[i] : 0);
+            h *= 1099511628211ull;
+        }
+    return h;
+}
+
+VariantPtr compile_batch(int threads, int dtype, const std::vector<BucketDesc>& b, const std::string& dir)
+{
+    VariantPtr v = compile_source(kBatchSource, sizeof kBatchSource, "batch.cu", batch_options(threads, dtype, b),
+                                  "ct_corr2d_batch", dir);
+    int64_t sm = 0;
+    for (const auto& d : b) sm = std::max(sm, bucket_smem(threads, d.cfg, d.fw, d.fh));
+    v->smem = sm;
+    return v;
+}
+
+ct_status launch_batch(Variant& v, int grid, int threads, const DevParams& prm, cudaStream_t s)
+{
+    ct_status st = load_variant(v);
+    if (st != CT_OK) return st;
+    DevParams copy = prm;
+    void* args[1] = {&copy};
+    cudaError_t e = cudaLaunchKernel((const void*)v.kern, dim3((unsigned)grid), dim3((unsigned)threads), args,
+                                     (size_t)v.smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchKernel(ct_corr2d_batch)");
+    return CT_OK;
+}
+
+int occupancy_grid(Variant& v, int threads, int blocks_per_sm, int64_t n_work)
+{
+    int dev = 0, sms = 1, nb = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (blocks_per_sm <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)v.kern, threads, (size_t)v.smem) !=
+                cudaSuccess ||
+            nb <= 0) {
+            cudaGetLastError();
+            nb = 1;
+        }
+    } else {
+        nb = blocks_per_sm;
+    }
+    return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nb * sms, n_work));
+}
+
+}  // namespace
+}  // namespace ct
+
+using namespace ct;
+
+struct ct_batch {
+    struct Bucket {
+        int fw = 0, fh = 0, side = 0;
+        std::vector<int> items;
+        TileCfg cfg;
+        double pp = NAN;
+    };
+    int dtype = CT_F32, threads = 256;
+    std::vector<ct_batch_item> items;
+    std::vector<int> item_bucket;
+    std::vector<int> filt_off;
+    std::vector<Bucket> buckets;
+    VariantPtr module;
+    void* d_probs = nullptr;
+    void* d_work = nullptr;
+    float* d_filters = nullptr;
+    unsigned* d_counter = nullptr;
+    int64_t n_work = 0;
+    int grid = 0;
+    cudaGraphExec_t exec = nullptr;
+    ct_batch_info info{};
+    ~ct_batch()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (d_probs) cudaFree(d_probs);
+        if (d_work) cudaFree(d_work);
+        if (d_filters) cudaFree(d_filters);
+        if (d_counter) cudaFree(d_counter);
+    }
+};
+
+namespace {
+
+int64_t tiles_of(const ct_batch_item& it, int threads, const TileCfg& c, int64_t* tx_out = nullptr)
+{
+    if (it.out_w <= 0 || it.out_h <= 0) {
+        if (tx_out) *tx_out = 0;
+        return 0;
+    }
+    const int64_t tw = tile_w(threads, c), th = tile_h(threads, c);
+    const int64_t tx = (it.out_w + tw - 1) / tw, ty = (it.out_h + th - 1) / th;
+    if (tx_out) *tx_out = tx;
+    return tx * ty;
+}
+
+DevProblem dev_problem(const ct_batch& B, int i, int bucket, const TileCfg& c)
+{
+    const ct_batch_item& it = B.items[(size_t)i];
+    DevProblem d{};
+    d.in = it.d_image;
+    d.out = it.d_out;
+    d.in_pitch = it.in_pitch;
+    d.out_pitch = it.out_pitch;
+    d.out_w = it.out_w;
+    d.out_h = it.out_h;
+    d.in_w = it.out_w + it.filter_w - 1;
+    d.in_h = it.out_h + it.filter_h - 1;
+    d.bucket = bucket;
+    int64_t tx = 0;
+    tiles_of(it, B.threads, c, &tx);
+    d.tiles_x = (int32_t)tx;
+    d.filt_off = B.filt_off[(size_t)i];
+    return d;
+}
+
+std::vector<TileCfg> bucket_candidates(int threads, int fw, int fh, int smem_limit)
+{
+    std::vector<TileCfg> out;
+    for (int bx : {16, 32, 64, 128}) {
+        if (bx > threads || threads % bx) continue;
+        for (int tx : {1, 2, 4})
+            for (int ty : {1, 2, 4, 8}) {
+                TileCfg c{bx, tx, ty};
+                if ((bx * tx) % 4) continue;
+                if (bucket_smem(threads, c, fw, fh) > smem_limit) continue;
+                out.push_back(c);
+            }
+    }
+    return out;
+}
+
+// Measures every candidate tile on (a sample of) the bucket's problems and
+// picks the one with the best objective.
+ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o, CompilePool& pool,
+                      cudaStream_t s, int smem_limit)
+{
+    std::vector<TileCfg> cand = bucket_candidates(B.threads, bk.fw, bk.fh, smem_limit);
+    if (cand.empty()) return fail(CT_ERR_INVALID_CONFIG, "no tile fits shared memory for filter %dx%d", bk.fw, bk.fh);
+    // sample of problems: sorted by size, evenly spaced, always the extremes
+    std::vector<int> its = bk.items;
+    std::sort(its.begin(), its.end(), [&](int a, int b) {
+        return (int64_t)B.items[(size_t)a].out_w * B.items[(size_t)a].out_h >
+               (int64_t)B.items[(size_t)b].out_w * B.items[(size_t)b].out_h;
+    });
+    its.erase(std::remove_if(its.begin(), its.end(),
+                             [&](int i) { return B.items[(size_t)i].out_w == 0 || B.items[(size_t)i].out_h == 0; }),
+              its.end());
+    if (its.empty()) return CT_OK;
+    const size_t cap = (size_t)(o.max_tune_items > 0 ? o.max_tune_items : 12);
+    std::vector<int> sample;
+    if (its.size() <= cap) {
+        sample = its;
+    } else {
+        for (size_t k = 0; k < cap; ++k) sample.push_back(its[k * (its.size() - 1) / (cap - 1)]);
+        sample.erase(std::unique(sample.begin(), sample.end()), sample.end());
+    }
+    // compile all candidates in parallel
+    std::vector<std::shared_future<VariantPtr>> futs;
+    std::vector<uint64_t> keys;
+    for (const auto& c : cand) {
+        std::vector<BucketDesc> one = {{bk.fw, bk.fh, c}};
+        const uint64_t key = options_key(batch_options(B.threads, B.dtype, one));
+        const std::string dir = pool.cache_dir();
+        const int thr = B.threads, dt = B.dtype;
+        keys.push_back(key);
+        futs.push_back(pool.request(key, [thr, dt, one, dir] { return compile_batch(thr, dt, one, dir); }));
+    }
+    int64_t max_tiles = 1;
+    for (const auto& c : cand)
+        for (int i : sample) max_tiles = std::max(max_tiles, tiles_of(B.items[(size_t)i], B.threads, c));
+    void* d_prob = nullptr;
+    void* d_work = nullptr;
+    unsigned* d_cnt = nullptr;
+    cudaEvent_t ev[2];
+    cudaEventCreate(&ev[0]);
+    cudaEventCreate(&ev[1]);
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(s);
+        if (d_prob) cudaFree(d_prob);
+        if (d_work) cudaFree(d_work);
+        if (d_cnt) cudaFree(d_cnt);
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        for (auto k : keys) pool.forget(k);
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_prob, sizeof(DevProblem))) != cudaSuccess ||
+        (e = cudaMalloc(&d_work, (size_t)max_tiles * sizeof(WorkItem))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&d_cnt, sizeof(unsigned))) != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "cudaMalloc(batch tuning scratch)");
+    }
+    const size_t nc = cand.size(), ni = sample.size();
+    std::vector<double> t((size_t)(nc * ni), std::numeric_limits<double>::infinity());
+    std::vector<WorkItem> work;
+    for (size_t ci = 0; ci < nc; ++ci) {
+        VariantPtr v = futs[ci].get();
+        if (!v || v->status != CT_OK) continue;
+        for (size_t ii = 0; ii < ni; ++ii) {
+            const int item = sample[ii];
+            const DevProblem dp = dev_problem(B, item, 0, cand[ci]);
+            const int64_t nt = tiles_of(B.items[(size_t)item], B.threads, cand[ci]);
+            work.resize((size_t)nt);
+            for (int64_t k = 0; k < nt; ++k) work[(size_t)k] = WorkItem{0u, (uint32_t)k};
+            cudaMemcpyAsync(d_prob, &dp, sizeof dp, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(d_work, work.data(), (size_t)nt * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
+            ct_status st = load_variant(*v);
+            if (st != CT_OK) break;
+            const int grid = occupancy_grid(*v, B.threads, o.blocks_per_sm, nt);
+            DevParams prm{d_prob, d_work, B.d_filters, d_cnt, (int32_t)nt, 0};
+            std::vector<float> ms;
+            bool ok = true;
+            for (int r = 0; r < 4 && ok; ++r) {
+                cudaMemsetAsync(d_cnt, 0, sizeof(unsigned), s);
+                cudaEventRecord(ev[0], s);
+                ok = launch_batch(*v, grid, B.threads, prm, s) == CT_OK;
+                cudaEventRecord(ev[1], s);
+                if ((e = cudaEventSynchronize(ev[1])) != cudaSuccess) {
+                    cleanup();
+                    return cuda_fail(e, "batch tuning launch");
+                }
+                float x = 0.f;
+                cudaEventElapsedTime(&x, ev[0], ev[1]);
+                if (r > 0) ms.push_back(x);   // the first launch is a warm-up
+            }
+            if (!ok) {
+                cudaGetLastError();
+                continue;
+            }
+            std::sort(ms.begin(), ms.end());
+            t[ci * ni + ii] = ms[ms.size() / 2];
+        }
+        unload_variant(*v);
+    }
+    cleanup();
+    // objective
+    size_t best = nc;
+    double best_score = -1.0;
+    double best_pp = NAN;
+    std::vector<double> pmax(ni, 0.0);
+    for (size_t ii = 0; ii < ni; ++ii)
+        for (size_t ci = 0; ci < nc; ++ci)
+            if (std::isfinite(t[ci * ni + ii])) pmax[ii] = std::max(pmax[ii], 1.0 / t[ci * ni + ii]);
+    for (size_t ci = 0; ci < nc; ++ci) {
+        double inv = 0.0, sum_t = 0.0;
+        bool all = true;
+        for (size_t ii = 0; ii < ni; ++ii) {
+            const double x = t[ci * ni + ii];
+            if (!std::isfinite(x)) {
+                all = false;
+                break;
+            }
+            inv += pmax[ii] * x;   // 1 / e_i with e_i = (1/x) / pmax_i
+            sum_t += x;
+        }
+        if (!all) continue;
+        const double pp = (double)ni / inv;
+        const double score = o.objective == 1 ? 1.0 / sum_t : pp;
+        if (score > best_score) {
+            best_score = score;
+            best = ci;
+            best_pp = pp;
+        }
+    }
+    if (best == nc) return fail(CT_ERR_LAUNCH, "no tile configuration ran for filter %dx%d", bk.fw, bk.fh);
+    bk.cfg = cand[best];
+    bk.pp = best_pp;
+    return CT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct_batch_opts* opts, ct_batch** out)
+{
+    if (!out) return fail(CT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n <= 0 || !items) return fail(CT_ERR_INVALID_ARG, "a batch needs at least one item");
+    ct_batch_opts o{};
+    if (opts) o = *opts;
+    if (o.dtype != CT_F32 && o.dtype != CT_BF16) return fail(CT_ERR_INVALID_ARG, "bad batch dtype %d", o.dtype);
+    const int threads = o.threads > 0 ? o.threads : 256;
+    if (threads % 16 || threads > 1024) return fail(CT_ERR_INVALID_ARG, "threads must be a multiple of 16, <= 1024");
+    const int split = o.side_split == 0 ? 512 : o.side_split;
+    ct_status st;
+    for (int i = 0; i < n; ++i) {
+        const ct_batch_item& it = items[i];
+        ct_problem p{it.out_w, it.out_h, it.filter_w, it.filter_h, it.in_pitch, it.out_pitch, o.dtype, 0};
+        if ((st = check_problem(&p)) != CT_OK || (st = check_buffers(p, it.d_image, it.h_filter, it.d_out)) != CT_OK)
+            return fail(st, "batch item %d: %s", i, last_error());
+    }
+    if ((st = require_device()) != CT_OK) return st;
+    const double t0 = now_ms();
+    auto B = std::unique_ptr<ct_batch>(new ct_batch());
+    B->dtype = o.dtype;
+    B->threads = threads;
+    B->items.assign(items, items + n);
+    // filters, widened to FP32, in one arena
+    std::vector<float> arena;
+    for (int i = 0; i < n; ++i) {
+        const ct_batch_item& it = items[i];
+        B->filt_off.push_back((int)arena.size());
+        const int nt = it.filter_w * it.filter_h;
+        for (int k = 0; k < nt; ++k) {
+            float v;
+            if (o.dtype == CT_F32) {
+                v = static_cast<const float*>(it.h_filter)[k];
+            } else {
+                const uint32_t u = (uint32_t) static_cast<const uint16_t*>(it.h_filter)[k] << 16;
+                memcpy(&v, &u, 4);
+            }
+            arena.push_back(v);
+        }
+    }
+    // buckets: filter size, then image side class
+    B->item_bucket.assign((size_t)n, -1);
+    for (int pass = 0; pass < 2; ++pass) {
+        B->buckets.clear();
+        for (int i = 0; i < n; ++i) {
+            const ct_batch_item& it = items[i];
+            const int side = (pass == 0 && split > 0 && std::max(it.out_w, it.out_h) >= split) ? 1 : 0;
+            int k = -1;
+            for (size_t b = 0; b < B->buckets.size(); ++b)
+                if (B->buckets[b].fw == it.filter_w && B->buckets[b].fh == it.filter_h && B->buckets[b].side == side)
+                    k = (int)b;
+            if (k < 0) {
+                ct_batch::Bucket nb;
+                nb.fw = it.filter_w;
+                nb.fh = it.filter_h;
+                nb.side = side;
+                B->buckets.push_back(nb);
+                k = (int)B->buckets.size() - 1;
+            }
+            B->buckets[(size_t)k].items.push_back(i);
+            B->item_bucket[(size_t)i] = k;
+        }
+        if (B->buckets.size() <= 16) break;
+    }
+    if (B->buckets.size() > 16) return fail(CT_ERR_UNSUPPORTED, "more than 16 filter sizes in one batch");
+    cudaError_t e;
+    if ((e = cudaMalloc((void**)&B->d_filters, std::max<size_t>(4, arena.size() * 4))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(batch filters)");
+    if ((e = cudaMemcpy(B->d_filters, arena.data(), arena.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "upload batch filters");
+    const int smem_limit = device_smem_limit();
+    cudaStream_t s = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreate");
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+    } sg{s};
+    double compile_cpu = 0.0;
+    const double tt0 = now_ms();
+    {
+        CompilePool pool(0, cache_dir_setting());
+        for (auto& bk : B->buckets) {
+            if (o.tune) {
+                if ((st = tune_bucket(*B, bk, o, pool, s, smem_limit)) != CT_OK) return st;
+            } else {
+                bk.cfg = TileCfg{32, 4, 4};
+                if (threads % 32) bk.cfg.bx = 16;
+                while (bucket_smem(threads, bk.cfg, bk.fw, bk.fh) > smem_limit && bk.cfg.ty > 1) bk.cfg.ty /= 2;
+            }
+        }
+    }
+    B->info.tune_ms = o.tune ? now_ms() - tt0 : 0.0;
+    // the persistent kernel with every bucket's tile routine
+    std::vector<BucketDesc> desc;
+    for (const auto& bk : B->buckets) desc.push_back({bk.fw, bk.fh, bk.cfg});
+    B->module = compile_batch(threads, o.dtype, desc, cache_dir_setting());
+    compile_cpu += B->module->compile_ms;
+    if (B->module->status != CT_OK) return fail(CT_ERR_COMPILE, "%s", B->module->error.c_str());
+    if (B->module->smem > smem_limit) return fail(CT_ERR_INVALID_CONFIG, "batch kernel needs too much shared memory");
+    if ((st = load_variant(*B->module)) != CT_OK) return st;
+    // problem table and work list: most expensive tiles first
+    std::vector<DevProblem> probs;
+    for (int i = 0; i < n; ++i) {
+        const int b = B->item_bucket[(size_t)i];
+        probs.push_back(dev_problem(*B, i, b, B->buckets[(size_t)b].cfg));
+    }
+    std::vector<int> border(B->buckets.size());
+    std::iota(border.begin(), border.end(), 0);
+    auto tile_cost = [&](int b) {
+        const auto& k = B->buckets[(size_t)b];
+        return (double)k.fw * k.fh * tile_w(threads, k.cfg) * tile_h(threads, k.cfg);
+    };
+    std::stable_sort(border.begin(), border.end(), [&](int a, int b) { return tile_cost(a) > tile_cost(b); });
+    std::vector<WorkItem> work;
+    for (int b : border) {
+        std::vector<int> its = B->buckets[(size_t)b].items;
+        std::stable_sort(its.begin(), its.end(), [&](int a, int c) {
+            return (int64_t)items[a].out_w * items[a].out_h > (int64_t)items[c].out_w * items[c].out_h;
+        });
+        for (int i : its) {
+            const int64_t nt = tiles_of(items[i], threads, B->buckets[(size_t)b].cfg);
+            for (int64_t k = 0; k < nt; ++k) work.push_back(WorkItem{(uint32_t)i, (uint32_t)k});
+        }
+    }
+    if (work.size() > (size_t)0x7fffffff) return fail(CT_ERR_UNSUPPORTED, "too many tiles in one batch");
+    B->n_work = (int64_t)work.size();
+    if ((e = cudaMalloc(&B->d_probs, probs.size() * sizeof(DevProblem))) != cudaSuccess ||
+        (e = cudaMalloc(&B->d_work, std::max<size_t>(1, work.size()) * sizeof(WorkItem))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&B->d_counter, sizeof(unsigned))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(batch tables)");
+    cudaMemcpyAsync(B->d_probs, probs.data(), probs.size() * sizeof(DevProblem), cudaMemcpyHostToDevice, s);
+    if (!work.empty())
+        cudaMemcpyAsync(B->d_work, work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "upload batch tables");
+    B->grid = occupancy_grid(*B->module, threads, o.blocks_per_sm, std::max<int64_t>(1, B->n_work));
+    // capture: counter reset + the persistent launch
+    DevParams prm{B->d_probs, B->d_work, B->d_filters, B->d_counter, (int32_t)B->n_work, 0};
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned), s);
+    st = launch_batch(*B->module, B->grid, threads, prm, s);
+    e = cudaStreamEndCapture(s, &g);
+    if (st != CT_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st != CT_OK ? st : cuda_fail(e, "cudaStreamEndCapture");
+    }
+    e = cudaGraphInstantiate(&B->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    B->info.n_items = n;
+    B->info.n_buckets = (int32_t)B->buckets.size();
+    B->info.n_work = B->n_work;
+    B->info.grid = B->grid;
+    B->info.threads = threads;
+    B->info.smem_bytes = (int32_t)B->module->smem;
+    B->info.regs = B->module->regs;
+    B->info.compile_cpu_ms = compile_cpu;
+    B->info.plan_ms = now_ms() - t0;
+    *out = B.release();
+    return CT_OK;
+}
+
+CT_API ct_status ct_batch_run(ct_batch* b, void* stream)
+{
+    if (!b || !b->exec) return fail(CT_ERR_INVALID_ARG, "batch is NULL");
+    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch(batch)");
+    return CT_OK;
+}
+
+CT_API ct_status ct_batch_info_get(const ct_batch* b, ct_batch_info* out)
+{
+    if (!b || !out) return fail(CT_ERR_INVALID_ARG, "batch and out must be non-NULL");
+    *out = b->info;
+    return CT_OK;
+}
+
+CT_API ct_status ct_batch_bucket(const ct_batch* b, int32_t k, int32_t* filter_w, int32_t* filter_h,
+                                 int32_t* n_items, ct_bucket_config* cfg, double* pp)
+{
+    if (!b) return fail(CT_ERR_INVALID_ARG, "batch is NULL");
+    if (k < 0 || k >= (int32_t)b->buckets.size()) return fail(CT_ERR_INVALID_ARG, "bucket %d out of range", k);
+    const auto& bk = b->buckets[(size_t)k];
+    if (filter_w) *filter_w = bk.fw;
+    if (filter_h) *filter_h = bk.fh;
+    if (n_items) *n_items = (int32_t)bk.items.size();
+    if (cfg) *cfg = ct_bucket_config{bk.cfg.bx, b->threads / bk.cfg.bx, bk.cfg.tx, bk.cfg.ty};
+    if (pp) *pp = bk.pp;
+    return CT_OK;
+}
+
+CT_API int32_t ct_batch_item_bucket(const ct_batch* b, int32_t i)
+{
+    if (!b || i < 0 || i >= (int32_t)b->item_bucket.size()) return -1;
+    return b->item_bucket[(size_t)i];
+}
+
+CT_API void ct_batch_free(ct_batch* b) { delete b; }
+
+}  // extern "C"

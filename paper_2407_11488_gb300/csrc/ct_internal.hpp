@@ -94,6 +94,7 @@ struct VariantKey {
 
 struct Variant {
     VariantKey key{};
+    std::string kname = "ct_corr2d";
     std::vector<char> cubin;
     std::string log;
     int status = CT_OK;
@@ -114,6 +115,10 @@ using VariantPtr = std::shared_ptr<Variant>;
 
 // Compiles with NVRTC, consulting the on-disk cache (thread safe; no device needed).
 VariantPtr compile_variant(const VariantKey& k, const std::string& cache_dir);
+VariantPtr compile_source(const char* src, size_t len, const char* prog_name, const std::vector<std::string>& opts,
+                          const std::string& kernel_name, const std::string& cache_dir);
+std::vector<std::string> nvrtc_base_options();
+void add_env_options(std::vector<std::string>& o);
 // Library-wide in-memory cache on top of compile_variant.
 VariantPtr get_variant(const VariantKey& k);
 void put_variant(const VariantPtr& v);
@@ -139,16 +144,26 @@ cudaError_t launch_l2_flush(void* buf, int64_t bytes, uint32_t salt, cudaStream_
 // ----------------------------------------------------------- compile pool ---
 class CompilePool {
 public:
+    using Job = std::function<VariantPtr()>;
     CompilePool(int nthreads, std::string cache_dir);
     ~CompilePool();
-    std::shared_future<VariantPtr> request(const VariantKey& k);
+    // urgent requests go to the front of the queue (or move there if queued)
+    std::shared_future<VariantPtr> request(const VariantKey& k, bool urgent = false);
+    std::shared_future<VariantPtr> request(uint64_t key, Job job, bool urgent = false);
     void forget(const VariantKey& k);
+    void forget(uint64_t key);
+    const std::string& cache_dir() const { return cache_dir_; }
 private:
+    struct Item {
+        uint64_t key;
+        Job job;
+        std::shared_ptr<std::promise<VariantPtr>> pr;
+    };
     void worker();
     std::string cache_dir_;
     std::mutex mu_;
     std::condition_variable cv_;
-    std::deque<std::pair<VariantKey, std::shared_ptr<std::promise<VariantPtr>>>> queue_;
+    std::deque<Item> queue_;
     std::unordered_map<uint64_t, std::shared_future<VariantPtr>> futures_;
     std::vector<std::thread> threads_;
     bool stop_ = false;

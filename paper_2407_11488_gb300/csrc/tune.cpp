@@ -25,36 +25,57 @@ CompilePool::~CompilePool()
     {
         std::lock_guard<std::mutex> g(mu_);
         stop_ = true;
-        for (auto& q : queue_) q.second->set_value(nullptr);
+        for (auto& q : queue_) q.pr->set_value(nullptr);
         queue_.clear();
     }
     cv_.notify_all();
     for (auto& t : threads_) t.join();
 }
 
-std::shared_future<VariantPtr> CompilePool::request(const VariantKey& k)
+std::shared_future<VariantPtr> CompilePool::request(const VariantKey& k, bool urgent)
+{
+    const std::string dir = cache_dir_;
+    return request(k.packed(), [k, dir] { return compile_variant(k, dir); }, urgent);
+}
+
+std::shared_future<VariantPtr> CompilePool::request(uint64_t key, Job job, bool urgent)
 {
     std::lock_guard<std::mutex> g(mu_);
-    auto it = futures_.find(k.packed());
-    if (it != futures_.end()) return it->second;
+    auto it = futures_.find(key);
+    if (it != futures_.end()) {
+        if (urgent) {
+            for (auto q = queue_.begin(); q != queue_.end(); ++q)
+                if (q->key == key) {
+                    Item item = *q;
+                    queue_.erase(q);
+                    queue_.push_front(item);
+                    break;
+                }
+        }
+        return it->second;
+    }
     auto pr = std::make_shared<std::promise<VariantPtr>>();
     auto fut = pr->get_future().share();
-    futures_[k.packed()] = fut;
-    queue_.emplace_back(k, pr);
+    futures_[key] = fut;
+    Item item{key, std::move(job), pr};
+    if (urgent) queue_.push_front(std::move(item));
+    else queue_.push_back(std::move(item));
     cv_.notify_one();
     return fut;
 }
 
-void CompilePool::forget(const VariantKey& k)
+void CompilePool::forget(const VariantKey& k) { forget(k.packed()); }
+
+void CompilePool::forget(uint64_t key)
 {
     std::lock_guard<std::mutex> g(mu_);
-    futures_.erase(k.packed());
+    futures_.erase(key);
 }
 
 void CompilePool::worker()
 {
     for (;;) {
-        std::pair<VariantKey, std::shared_ptr<std::promise<VariantPtr>>> job;
+        Item job;
         {
             std::unique_lock<std::mutex> g(mu_);
             cv_.wait(g, [this] { return stop_ || !queue_.empty(); });
@@ -62,7 +83,7 @@ void CompilePool::worker()
             job = queue_.front();
             queue_.pop_front();
         }
-        job.second->set_value(compile_variant(job.first, cache_dir_));
+        job.pr->set_value(job.job());
     }
 }
 
@@ -95,7 +116,7 @@ static void summarize(std::vector<double>& t, Measure& m)
 class Evaluator {
 public:
     virtual ~Evaluator() = default;
-    virtual void prefetch(const Entry&) {}
+    virtual void prefetch(const Entry&, bool urgent = false) { (void)urgent; }
     virtual Measure eval(const Entry& e) = 0;
     double compile_wait_ms = 0, compile_cpu_ms = 0, bench_ms = 0;
     bool abort = false;   // set after an unrecoverable device error
@@ -141,7 +162,7 @@ public:
         for (auto& e : ev_) cudaEventDestroy(e);
     }
     VariantKey key(const Entry& e) const { return VariantKey{e.cfg, p_.filter_w, p_.filter_h, p_.dtype}; }
-    void prefetch(const Entry& e) override { pool_.request(key(e)); }
+    void prefetch(const Entry& e, bool urgent) override { pool_.request(key(e), urgent); }
 
     Measure eval(const Entry& e) override
     {
@@ -403,10 +424,10 @@ public:
     bool visited(int64_t idx) const { return row_of_.count(idx) != 0; }
     size_t n_rows() const { return rows.size(); }
 
-    void prefetch(const Entry& e)
+    void prefetch(const Entry& e, bool urgent = false)
     {
         if (!visited(e.index) && !resume_.count(VariantKey{e.cfg, p_.filter_w, p_.filter_h, p_.dtype}.packed()))
-            ev_.prefetch(e);
+            ev_.prefetch(e, urgent);
     }
 
     // Measures e once (memoised); returns its median time or +inf on failure.
@@ -505,67 +526,89 @@ static std::vector<int64_t> neighbours(const Space& s, const Driver& d, const ct
 // objective normalised by the first measured time, temperature cooled
 // geometrically from 1 to 1e-3 over the evaluation budget, Metropolis
 // acceptance, restart from the best point after budget/10 fresh evaluations
-// without improvement, memoised measurements.
+// without improvement, memoised measurements.  `chains` walkers advance in
+// lock step: each round proposes one candidate per walker, the candidates are
+// compiled together (urgent requests), then measured one after another, so a
+// round costs about one compile latency instead of one per walker.
 static void run_anneal(Driver& d, const Space& s, const std::vector<Entry>& valid, int64_t budget, uint64_t seed,
-                       const bool* stop)
+                       int chains, const bool* stop)
 {
     Rng rng(seed ^ 0xA5A5A5A5ull);
-    const Entry* cur = &valid[rng.below(valid.size())];
-    double f_first = d.evaluate(*cur);
-    double f_cur = f_first;
-    const Entry* best = cur;
-    double f_best = f_cur;
+    chains = std::max(1, std::min<int>(chains, (int)std::max<int64_t>(1, budget / 8)));
+    struct Walker {
+        const Entry* cur = nullptr;
+        double f = std::numeric_limits<double>::infinity();
+        int64_t idle = 0;
+    };
+    std::vector<Walker> w((size_t)chains);
+    for (auto& x : w) x.cur = &valid[rng.below(valid.size())];
+    for (auto& x : w) d.prefetch(*x.cur, true);
+    double f_first = std::numeric_limits<double>::infinity();
+    const Entry* best = w[0].cur;
+    double f_best = std::numeric_limits<double>::infinity();
+    for (auto& x : w) {
+        x.f = d.evaluate(*x.cur);
+        if (!std::isfinite(f_first) && std::isfinite(x.f)) f_first = x.f;
+        if (x.f < f_best) { best = x.cur; f_best = x.f; }
+    }
     const double T0 = 1.0, T1 = 1e-3;
     const int64_t stall_limit = std::max<int64_t>(1, budget / 10);
-    int64_t stall = 0, idle = 0, steps = 0;
+    int64_t stall = 0, steps = 0;
     const int64_t max_steps = 200 * budget + 1000;
-    while ((int64_t)d.n_rows() < budget && steps++ < max_steps) {
+    std::vector<const Entry*> cand((size_t)chains);
+    while ((int64_t)d.n_rows() < budget && steps < max_steps) {
         if (stop && *stop) return;
-        if (!std::isfinite(f_first)) {
-            // the first point failed: normalise by the first success instead
-            const Entry* e = &valid[rng.below(valid.size())];
-            f_first = d.evaluate(*e);
-            cur = e;
-            f_cur = f_first;
-            if (f_cur < f_best) { best = cur; f_best = f_cur; }
-            continue;
-        }
-        std::vector<int64_t> nb = neighbours(s, d, cur->cfg);
-        bool all_seen = true;
-        for (int64_t i : nb)
-            if (!d.visited(i)) {
-                d.prefetch(d.entry(i));
-                all_seen = false;
+        ++steps;
+        for (size_t m = 0; m < w.size(); ++m) {
+            Walker& x = w[m];
+            if (!std::isfinite(x.f)) {   // a walker on a failing point jumps
+                x.cur = &valid[rng.below(valid.size())];
+                cand[m] = x.cur;
+                continue;
             }
-        const Entry* cand;
-        if (nb.empty() || (all_seen && idle > 2 * (int64_t)nb.size())) {
-            // stuck in an explored region: jump to a random unvisited point
-            std::vector<const Entry*> fresh;
-            for (const auto& e : valid)
-                if (!d.visited(e.index)) fresh.push_back(&e);
-            if (fresh.empty()) return;
-            cand = fresh[rng.below(fresh.size())];
-            idle = 0;
-        } else {
-            cand = &d.entry(nb[rng.below(nb.size())]);
+            std::vector<int64_t> nb = neighbours(s, d, x.cur->cfg);
+            bool all_seen = true;
+            for (int64_t i : nb) all_seen = all_seen && d.visited(i);
+            if (nb.empty() || (all_seen && x.idle > 2 * (int64_t)nb.size())) {
+                std::vector<const Entry*> fresh;
+                for (const auto& e : valid)
+                    if (!d.visited(e.index)) fresh.push_back(&e);
+                if (fresh.empty()) return;
+                cand[m] = fresh[rng.below(fresh.size())];
+                x.idle = 0;
+            } else {
+                cand[m] = &d.entry(nb[rng.below(nb.size())]);
+            }
         }
-        bool fresh_eval = false;
-        const double f_c = d.evaluate(*cand, &fresh_eval);
-        idle = fresh_eval ? 0 : idle + 1;
-        const double T = T0 * std::pow(T1 / T0, std::min(1.0, (double)d.n_rows() / (double)budget));
-        const double delta = (f_c - f_cur) / f_first;
-        if (std::isfinite(f_c) && (delta < 0 || rng.uniform() < std::exp(-delta / T))) {
-            cur = cand;
-            f_cur = f_c;
-        }
-        if (f_c < f_best) {
-            best = cand;
-            f_best = f_c;
-            stall = 0;
-        } else if (fresh_eval && ++stall >= stall_limit) {
-            cur = best;
-            f_cur = f_best;
-            stall = 0;
+        for (const Entry* c : cand) d.prefetch(*c, true);
+        for (size_t m = 0; m < w.size() && (int64_t)d.n_rows() < budget; ++m) {
+            Walker& x = w[m];
+            bool fresh_eval = false;
+            const double f_c = d.evaluate(*cand[m], &fresh_eval);
+            if (!std::isfinite(f_first) && std::isfinite(f_c)) f_first = f_c;
+            x.idle = fresh_eval ? 0 : x.idle + 1;
+            if (!std::isfinite(x.f)) {
+                x.cur = cand[m];
+                x.f = f_c;
+            } else if (std::isfinite(f_c)) {
+                const double T = T0 * std::pow(T1 / T0, std::min(1.0, (double)d.n_rows() / (double)budget));
+                const double delta = (f_c - x.f) / f_first;
+                if (delta < 0 || rng.uniform() < std::exp(-delta / T)) {
+                    x.cur = cand[m];
+                    x.f = f_c;
+                }
+            }
+            if (f_c < f_best) {
+                best = cand[m];
+                f_best = f_c;
+                stall = 0;
+            } else if (fresh_eval && ++stall >= stall_limit) {
+                for (auto& y : w) {
+                    y.cur = best;
+                    y.f = f_best;
+                }
+                stall = 0;
+            }
         }
     }
 }
@@ -596,7 +639,7 @@ static ct_status run_strategy(const ct_problem& p, const Space& s, ct_strategy s
     } else if (st == CT_RANDOM) {
         run_list(d, random_sample(valid, budget, o.seed), window, stop);
     } else if (st == CT_ANNEAL) {
-        run_anneal(d, s, valid, budget, o.seed, stop);
+        run_anneal(d, s, valid, budget, o.seed, o.anneal_chains > 0 ? o.anneal_chains : 1, stop);
     } else {
         return fail(CT_ERR_INVALID_ARG, "unknown strategy %d", (int)st);
     }

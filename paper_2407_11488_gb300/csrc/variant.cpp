@@ -50,9 +50,22 @@ Variant::~Variant()
     if (lib) cudaLibraryUnload(lib);
 }
 
+std::vector<std::string> nvrtc_base_options();
+
+// Extra NVRTC options from the environment (space separated), e.g. to inject
+// a compile failure when testing how failures are recorded.
+void add_env_options(std::vector<std::string>& o)
+{
+    if (const char* extra = getenv("CONVTUNE_NVRTC_EXTRA")) {
+        std::istringstream is(extra);
+        std::string tok;
+        while (is >> tok) o.push_back(tok);
+    }
+}
+
 static std::vector<std::string> nvrtc_options(const VariantKey& k)
 {
-    std::vector<std::string> o = {kArch, "--std=c++17", "--ptxas-options=-v", "-lineinfo"};
+    std::vector<std::string> o = nvrtc_base_options();
     auto def = [&](const char* n, int v) { o.push_back(std::string("-D") + n + "=" + std::to_string(v)); };
     def("CT_BX", k.cfg.block_x);
     def("CT_BY", k.cfg.block_y);
@@ -63,13 +76,7 @@ static std::vector<std::string> nvrtc_options(const VariantKey& k)
     def("CT_FW", k.fw);
     def("CT_FH", k.fh);
     def("CT_DTYPE", k.dtype);
-    // Extra NVRTC options from the environment (space separated), e.g. to
-    // inject a compile failure when testing how failures are recorded.
-    if (const char* extra = getenv("CONVTUNE_NVRTC_EXTRA")) {
-        std::istringstream is(extra);
-        std::string tok;
-        while (is >> tok) o.push_back(tok);
-    }
+    add_env_options(o);
     return o;
 }
 
@@ -83,11 +90,11 @@ static uint64_t fnv1a(const void* data, size_t n, uint64_t h = 14695981039346656
     return h;
 }
 
-static uint64_t cache_hash(const std::vector<std::string>& opts)
+static uint64_t cache_hash(const char* src, size_t len, const std::vector<std::string>& opts)
 {
     int maj = 0, min = 0;
     nvrtcVersion(&maj, &min);
-    uint64_t h = fnv1a(kCorr2dSource, sizeof kCorr2dSource);
+    uint64_t h = fnv1a(src, len);
     for (const auto& s : opts) h = fnv1a(s.c_str(), s.size() + 1, h);
     int v[2] = {maj, min};
     return fnv1a(v, sizeof v, h);
@@ -142,19 +149,20 @@ static void mkdirs(const std::string& dir)
     }
 }
 
-VariantPtr compile_variant(const VariantKey& k, const std::string& cache_dir)
+std::vector<std::string> nvrtc_base_options()
+{
+    return {kArch, "--std=c++17", "--ptxas-options=-v", "-lineinfo"};
+}
+
+VariantPtr compile_source(const char* src, size_t len, const char* prog_name, const std::vector<std::string>& opts,
+                          const std::string& kernel_name, const std::string& cache_dir)
 {
     auto v = std::make_shared<Variant>();
-    v->key = k;
-    ct_problem p{};
-    p.filter_w = k.fw;
-    p.filter_h = k.fh;
-    v->smem = smem_bytes(p, k.cfg);
-    const std::vector<std::string> opts = nvrtc_options(k);
+    v->kname = kernel_name;
     std::string base;
     if (!cache_dir.empty()) {
         char hex[32];
-        snprintf(hex, sizeof hex, "%016llx", (unsigned long long)cache_hash(opts));
+        snprintf(hex, sizeof hex, "%016llx", (unsigned long long)cache_hash(src, len, opts));
         base = cache_dir + "/ct-" + hex;
         std::string bin, log;
         if (read_file(base + ".cubin", bin) && read_file(base + ".log", log) && !bin.empty()) {
@@ -167,14 +175,14 @@ VariantPtr compile_variant(const VariantKey& k, const std::string& cache_dir)
     }
     const double t0 = now_ms();
     nvrtcProgram prog = nullptr;
-    nvrtcResult r = nvrtcCreateProgram(&prog, kCorr2dSource, "corr2d.cu", 0, nullptr, nullptr);
+    nvrtcResult r = nvrtcCreateProgram(&prog, src, prog_name, 0, nullptr, nullptr);
     if (r != NVRTC_SUCCESS) {
         v->status = CT_ERR_COMPILE;
         v->error = std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(r);
         return v;
     }
     std::vector<const char*> co;
-    for (const auto& s : opts) co.push_back(s.c_str());
+    for (const auto& o : opts) co.push_back(o.c_str());
     r = nvrtcCompileProgram(prog, (int)co.size(), co.data());
     size_t ls = 0;
     nvrtcGetProgramLogSize(prog, &ls);
@@ -184,7 +192,7 @@ VariantPtr compile_variant(const VariantKey& k, const std::string& cache_dir)
     v->log = log;
     if (r != NVRTC_SUCCESS) {
         v->status = CT_ERR_COMPILE;
-        v->error = std::string("NVRTC failed for ") + k.describe() + ": " + nvrtcGetErrorString(r) + "\n" + log;
+        v->error = std::string("NVRTC failed for ") + prog_name + ": " + nvrtcGetErrorString(r) + "\n" + log;
         nvrtcDestroyProgram(&prog);
         return v;
     }
@@ -200,6 +208,19 @@ VariantPtr compile_variant(const VariantKey& k, const std::string& cache_dir)
         write_file_atomic(base + ".log", v->log.data(), v->log.size());
         write_file_atomic(base + ".cubin", v->cubin.data(), v->cubin.size());
     }
+    return v;
+}
+
+VariantPtr compile_variant(const VariantKey& k, const std::string& cache_dir)
+{
+    const std::vector<std::string> opts = nvrtc_options(k);
+    VariantPtr v = compile_source(kCorr2dSource, sizeof kCorr2dSource, "corr2d.cu", opts, "ct_corr2d", cache_dir);
+    v->key = k;
+    ct_problem p{};
+    p.filter_w = k.fw;
+    p.filter_h = k.fh;
+    v->smem = smem_bytes(p, k.cfg);
+    if (v->status != CT_OK) v->error = "NVRTC failed for " + k.describe() + ": " + v->error;
     return v;
 }
 
@@ -304,7 +325,7 @@ ct_status load_variant(Variant& v)
             v.lib = nullptr;
             return cuda_fail(e, "cudaLibraryLoadData");
         }
-        e = cudaLibraryGetKernel(&v.kern, v.lib, "ct_corr2d");
+        e = cudaLibraryGetKernel(&v.kern, v.lib, v.kname.c_str());
         if (e != cudaSuccess) return cuda_fail(e, "cudaLibraryGetKernel");
     }
     if (v.loaded_device != dev || v.smem_attr != v.smem) {

@@ -253,3 +253,16 @@ def test_resume_uses_recorded_rows(ctlib, tmp_path):
     p2 = ctlib.make_problem(128, 256, 5, 5)
     third = ctlib.tune_replay(p2, "small", "brute", times * 2.0, resume_path=path)
     assert third.rows[0]["t_med_ms"] == pytest.approx(times[0] * 2.0)
+
+
+def test_batch_validation_without_gpu(ctlib):
+    import ctypes
+    items = (ctlib.BatchItem * 1)()
+    items[0] = ctlib.BatchItem(16, 16, 16, 64, 64, 5, 5, 66, 64)      # pitch 66 is not 16-byte aligned
+    h = ctlib.vp()
+    st = ctlib.lib().ct_batch_create(items, 1, None, ctypes.byref(h))
+    assert st == -1 and b"item 0" in ctlib.lib().ct_last_error()
+    assert ctlib.lib().ct_batch_create(items, 0, None, ctypes.byref(h)) == -1
+    if NO_GPU:
+        items[0] = ctlib.BatchItem(16, 16, 16, 64, 64, 5, 5, 68, 64)
+        assert ctlib.lib().ct_batch_create(items, 1, None, ctypes.byref(h)) == -8
