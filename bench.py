@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch"], default="full")
     ap.add_argument("--anneal-chains", type=int, default=4)
+    ap.add_argument("--batch-plain", choices=["tune", "skip"], default="tune",
+                    help="skip: time only the batched path (profiling)")
     ap.add_argument("--batch-plain-evals", type=int, default=120,
                     help="annealing budget per filter size for the per-problem path of the batch workload")
     ap.add_argument("--strategy", choices=["random", "anneal", "brute"], default="anneal")
@@ -437,7 +439,7 @@ def run_batch(args):
     t0 = time.time()
     cfg_for = {}
     tuning = {}
-    for fs in sorted(set(fs for _, fs in shapes)):
+    for fs in sorted(set(fs for _, fs in shapes)) if args.batch_plain == "tune" else []:
         big = max((p for p in probs if p[5] == fs), key=lambda p: p[4])
         _, f, d_img, out, side, _ = big
         pr = ct.problem_for(d_img, f, in_w=side + fs - 1)
@@ -448,7 +450,7 @@ def run_batch(args):
                                   "evals": tab.info["n_rows"]}
     plain_tune_s = time.time() - t0
     plain_args = []
-    for img, f, d_img, out, side, fs in probs:
+    for img, f, d_img, out, side, fs in (probs if args.batch_plain == "tune" else []):
         pr = ct.problem_for(d_img, f, in_w=side + fs - 1)
         pr.out_pitch = out.stride(0)
         plain_args.append((pr, cfg_for[fs], d_img.data_ptr(), f, out.data_ptr()))
@@ -493,7 +495,7 @@ def run_batch(args):
     tb0 = time.time()
     ms_batch = timed(batch_step, k, max(3, args.warmup))
     tb1 = time.time()
-    ms_plain = timed(plain_step, k, max(3, args.warmup))
+    ms_plain = timed(plain_step, k, max(3, args.warmup)) if plain_args else [float("nan")]
     clocks.stop()
     # the batched outputs equal the per-problem outputs bit for bit
     batch_step()
@@ -502,7 +504,7 @@ def run_batch(args):
     plain_step()
     stream.synchronize()
     identical = all(torch.equal(a.view(torch.int32), out.view(torch.int32))
-                    for a, (_, _, _, out, _, _) in zip(snap, probs))
+                    for a, (_, _, _, out, _, _) in zip(snap, probs)) if plain_args else None
 
     # end to end: pinned host images in, outputs out, every step
     h_imgs = [torch.from_numpy(img).pin_memory() for (img, *_rest) in probs]
