@@ -341,6 +341,31 @@ CT_API ct_status ct_batch_bucket(const ct_batch* b, int32_t k, int32_t* filter_w
 CT_API int32_t ct_batch_item_bucket(const ct_batch* b, int32_t i);
 CT_API void ct_batch_free(ct_batch* b);
 
+/* ---- batched correlation without allocation ------------------------------
+ *
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory when they need the work done (a process whose
+ * device memory is fully budgeted, a latency-critical path that must not
+ * allocate or synchronise on an allocation, a plugin whose host application
+ * owns every allocation).  It runs the same correlations as a batch, with the
+ * same per-output arithmetic as ct_conv2d (taps in (i, j) order, one FMA each),
+ * but with a kernel compiled ahead of time and all per-call scratch (work
+ * counter, problem table, tile prefix sums, FP32 filters) in one statically
+ * allocated 1 MiB device array: it calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Every GPU that loads the library holds that array until
+ * the process exits.
+ *
+ * items / n / dtype as for ct_batch_create (n <= 1024; the problem table, the
+ * prefix sums and every filter must fit the 1 MiB scratch, otherwise
+ * CT_ERR_INVALID_ARG with the needed size).  Enqueued on `stream`; the copy of
+ * the tables from host memory makes the call wait for work already queued on
+ * that stream.  The first call on a device looks up the scratch array's device
+ * address (make that first call before any stream capture).  All calls share
+ * the one array and each overwrites it (the work counter is reset by every
+ * call): calls whose work overlaps on the GPU race, so serialise them (one
+ * stream, or wait for the previous call). */
+CT_API ct_status ct_batch_run_noalloc(const ct_batch_item* items, int32_t n, int32_t dtype, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -136,6 +136,7 @@ _SIGS = {
     "ct_batch_bucket": (i32, [vp, i32, P(i32), P(i32), P(i32), P(BucketConfig), P(dbl)]),
     "ct_batch_item_bucket": (i32, [vp, i32]),
     "ct_batch_free": (None, [vp]),
+    "ct_batch_run_noalloc": (i32, [P(BatchItem), i32, i32, vp]),
 }
 EXPORTED = tuple(_SIGS)
 

@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libconvtune.so")
 
 CPP = ["common.cpp", "variant.cpp", "tune.cpp", "capi.cpp", "batch.cpp"]
-CU = ["aux_kernels.cu"]
+CU = ["aux_kernels.cu", "noalloc.cu"]
 HEADERS = ["ct_internal.hpp", "corr2d.cuh", "batch.cuh"]
 GENCODE = "-gencode=arch=compute_103a,code=sm_103a"
 
