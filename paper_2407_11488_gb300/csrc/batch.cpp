@@ -50,11 +50,18 @@ struct BucketDesc {
 int64_t tile_w(int threads, const TileCfg& c) { (void)threads; return (int64_t)c.bx * c.tx; }
 int64_t tile_h(int threads, const TileCfg& c) { return (int64_t)(threads / c.bx) * c.ty; }
 
-int64_t bucket_smem(int threads, const TileCfg& c, int fw, int fh)
+// floats of one item buffer (taps + halo), a multiple of 4
+int64_t bucket_buf_floats(int threads, const TileCfg& c, int fw, int fh)
 {
     const int64_t hh = tile_h(threads, c) + fh - 1;
     const int64_t sw = round_up(tile_w(threads, c) + fw - 1, 4);
-    return (fh * round_up(fw, 4) + hh * sw) * 4;
+    return round_up(fh * round_up(fw, 4) + hh * sw, 4);
+}
+
+// dynamic shared memory of the kernel: two item buffers
+int64_t bucket_smem(int threads, const TileCfg& c, int fw, int fh)
+{
+    return 2 * 4 * bucket_buf_floats(threads, c, fw, fh);
 }
 
 std::vector<std::string> batch_options(int threads, int dtype, const std::vector<BucketDesc>& b)
@@ -64,6 +71,9 @@ std::vector<std::string> batch_options(int threads, int dtype, const std::vector
     def("CT_NT", threads);
     def("CT_DTYPE", dtype);
     def("CT_NB", (int)b.size());
+    int64_t buf = 4;
+    for (const auto& d : b) buf = std::max(buf, bucket_buf_floats(threads, d.cfg, d.fw, d.fh));
+    def("CT_BUF_FLOATS", (int)buf);
     for (size_t k = 0; k < b.size(); ++k) {
         const std::string p = "CT_B" + std::to_string(k) + "_";
         def(p + "BX", b[k].cfg.bx);
@@ -380,22 +390,27 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
     B->dtype = o.dtype;
     B->threads = threads;
     B->items.assign(items, items + n);
-    // filters, widened to FP32, in one arena
+    // filters, widened to FP32, rows zero-padded to a multiple of 4 taps, in
+    // one arena (every filter starts on a 16-byte boundary)
     std::vector<float> arena;
     for (int i = 0; i < n; ++i) {
         const ct_batch_item& it = items[i];
         B->filt_off.push_back((int)arena.size());
-        const int nt = it.filter_w * it.filter_h;
-        for (int k = 0; k < nt; ++k) {
-            float v;
-            if (o.dtype == CT_F32) {
-                v = static_cast<const float*>(it.h_filter)[k];
-            } else {
-                const uint32_t u = (uint32_t) static_cast<const uint16_t*>(it.h_filter)[k] << 16;
-                memcpy(&v, &u, 4);
+        const int fwp = (int)round_up(it.filter_w, 4);
+        for (int r = 0; r < it.filter_h; ++r)
+            for (int c = 0; c < fwp; ++c) {
+                float v = 0.0f;
+                if (c < it.filter_w) {
+                    const int k = r * it.filter_w + c;
+                    if (o.dtype == CT_F32) {
+                        v = static_cast<const float*>(it.h_filter)[k];
+                    } else {
+                        const uint32_t u = (uint32_t) static_cast<const uint16_t*>(it.h_filter)[k] << 16;
+                        memcpy(&v, &u, 4);
+                    }
+                }
+                arena.push_back(v);
             }
-            arena.push_back(v);
-        }
     }
     // buckets: filter size, then image side class
     B->item_bucket.assign((size_t)n, -1);

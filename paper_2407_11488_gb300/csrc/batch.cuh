@@ -5,9 +5,10 @@
 // a bucket (same filter size, similar image size); each bucket has its own
 // compile-time tile routine (filter size, block shape, register tile), chosen
 // by the library's tuner, and one launch holds all of them.  Each block
-// repeatedly takes the next work item (problem, tile) from a global counter,
-// stages the problem's filter taps and the tile's input halo in shared
-// memory, computes the tile and stores it.
+// repeatedly takes the next work item (problem, tile) from a global counter;
+// the problem's filter taps and the tile's input halo are copied into one of
+// two shared-memory buffers with cp.async while the block computes the
+// previous item from the other buffer.
 //
 // The per-output arithmetic is that of the single-problem kernel: one FP32
 // fused multiply-add per tap, taps added in (i, j) order, so results are
@@ -16,7 +17,11 @@
 // Macros: CT_NT (threads per block), CT_DTYPE (0 FP32, 1 BF16 image),
 // CT_NB (buckets), and for every bucket b < CT_NB: CT_B<b>_BX (block width;
 // block height = CT_NT / BX), CT_B<b>_TX, CT_B<b>_TY (register tile),
-// CT_B<b>_FW, CT_B<b>_FH (filter).
+// CT_B<b>_FW, CT_B<b>_FH (filter); CT_BUF_FLOATS, the size of one item
+// buffer (the largest bucket's, a multiple of 4 floats).
+//
+// Filters are stored FP32, each row padded with zeros to a multiple of 4
+// taps, every filter starting on a 16-byte boundary.
 
 #ifndef CT_DTYPE
 #define CT_DTYPE 0
@@ -41,39 +46,48 @@ struct CtBatchProblem {
 struct CtBatchParams {
     const CtBatchProblem* probs;
     const uint2* work;       // (problem index, tile index)
-    const float* filters;    // all filters, FP32, row-major, problem p at filt_off
+    const float* filters;    // all filters, FP32, rows padded to 4 taps, problem p at filt_off
     unsigned int* counter;   // next work item; zero before the launch
     int n_work;
 };
 
 __device__ __forceinline__ constexpr int ct_rup(int v, int m) { return (v + m - 1) / m * m; }
 
-template <int BX, int TX, int TY, int FW, int FH>
-__device__ __forceinline__ void ct_batch_tile(const CtBatchProblem& pr, const float* __restrict__ filters, int tile,
-                                              float* sm)
+__device__ __forceinline__ void ct_cp16(float* dst, const void* src, bool valid)
 {
-    constexpr int BY = CT_NT / BX;
-    constexpr int TW = BX * TX, TH = BY * TY;
-    constexpr int HW = TW + FW - 1, HH = TH + FH - 1;
-    constexpr int SW = ct_rup(HW, 4);
-    constexpr int FWP = ct_rup(FW, 4);
-    constexpr int VW = (TX % 4 == 0) ? 4 : ((TX % 2 == 0) ? 2 : 1);
-    constexpr int WW = TX + FW - 1;
-    constexpr int WWV = ct_rup(WW, VW);
-    float* taps = sm;
-    float* halo = sm + FH * FWP;
+    const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void ct_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void ct_cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
-    const int tid = threadIdx.x;
-    const int bxi = tile % pr.tiles_x, byi = tile / pr.tiles_x;
-    const int gx0 = bxi * TW, gy0 = byi * TH;
+// Shared-memory buffer of one work item: filter taps (FH rows of FWP floats,
+// zero padded), then the input tile plus halo (HH rows of SW floats).
+template <int BX, int TX, int TY, int FW, int FH>
+struct CtTile {
+    static constexpr int BY = CT_NT / BX;
+    static constexpr int TW = BX * TX, TH = BY * TY;
+    static constexpr int HW = TW + FW - 1, HH = TH + FH - 1;
+    static constexpr int SW = ct_rup(HW, 4);
+    static constexpr int FWP = ct_rup(FW, 4);
+    static constexpr int VW = (TX % 4 == 0) ? 4 : ((TX % 2 == 0) ? 2 : 1);
+    static constexpr int WW = TX + FW - 1;
+    static constexpr int WWV = ct_rup(WW, VW);
 
-    // filter taps, rows padded to a multiple of 4 with zeros
-    for (int k = tid; k < FH * FWP; k += CT_NT) {
-        const int i = k / FWP, j = k - i * FWP;
-        taps[k] = j < FW ? __ldg(filters + pr.filt_off + i * FW + j) : 0.0f;
-    }
-    // input tile plus halo in 4-element chunks (16 bytes FP32, 8 bytes BF16)
+    // Starts the copies of one item into buf (asynchronous for FP32 images).
+    static __device__ __forceinline__ void stage(const CtBatchProblem& pr, const float* __restrict__ filters,
+                                                 int tile, float* buf)
     {
+        const int tid = threadIdx.x;
+        float* taps = buf;
+        float* halo = buf + FH * FWP;
+        const int gx0 = (tile % pr.tiles_x) * TW, gy0 = (tile / pr.tiles_x) * TH;
+        for (int k = tid; k < FH * FWP / 4; k += CT_NT) ct_cp16(taps + 4 * k, filters + pr.filt_off + 4 * k, true);
         constexpr int CH = SW / 4;
         constexpr int NCH = HH * CH;
 #pragma unroll 4
@@ -81,156 +95,244 @@ __device__ __forceinline__ void ct_batch_tile(const CtBatchProblem& pr, const fl
             const int r = idx / CH;
             const int c = (idx - r * CH) * 4;
             const int yy = gy0 + r, xx = gx0 + c;
-            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (yy < pr.in_h && xx < pr.in_w) {
-                const ct_in_t* src = pr.in + (ct_i64)yy * pr.in_pitch + xx;
+            const bool ok = yy < pr.in_h && xx < pr.in_w;
 #if CT_DTYPE == 0
-                v = __ldg(reinterpret_cast<const float4*>(src));
+            ct_cp16(halo + r * SW + c, ok ? (const void*)(pr.in + (ct_i64)yy * pr.in_pitch + xx) : (const void*)pr.in,
+                    ok);
 #else
-                const uint2 u = __ldg(reinterpret_cast<const uint2*>(src));
+            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (ok) {
+                const uint2 u = __ldg(reinterpret_cast<const uint2*>(pr.in + (ct_i64)yy * pr.in_pitch + xx));
                 v = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
                                 __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
-#endif
             }
             *reinterpret_cast<float4*>(halo + r * SW + c) = v;
+#endif
         }
     }
-    __syncthreads();
 
-    const int lx = (tid % BX) * TX, ly = (tid / BX) * TY;
-    float acc[TY][TX];
+    // Computes and stores one item whose taps and halo are in buf.
+    static __device__ __forceinline__ void compute(const CtBatchProblem& pr, int tile, const float* buf)
+    {
+        const int tid = threadIdx.x;
+        const float* taps = buf;
+        const float* halo = buf + FH * FWP;
+        const int gx0 = (tile % pr.tiles_x) * TW, gy0 = (tile / pr.tiles_x) * TH;
+        const int lx = (tid % BX) * TX, ly = (tid / BX) * TY;
+        float acc[TY][TX];
 #pragma unroll
-    for (int ty = 0; ty < TY; ++ty)
+        for (int ty = 0; ty < TY; ++ty)
 #pragma unroll
-        for (int tx = 0; tx < TX; ++tx) acc[ty][tx] = 0.0f;
+            for (int tx = 0; tx < TX; ++tx) acc[ty][tx] = 0.0f;
 
 #pragma unroll 1
-    for (int i = 0; i < FH; ++i) {
-        float f[FWP];
+        for (int i = 0; i < FH; ++i) {
+            float f[FWP];
 #pragma unroll
-        for (int q = 0; q < FWP; q += 4) {
-            const float4 t = *reinterpret_cast<const float4*>(taps + i * FWP + q);
-            f[q] = t.x; f[q + 1] = t.y; f[q + 2] = t.z; f[q + 3] = t.w;
-        }
-#pragma unroll
-        for (int ty = 0; ty < TY; ++ty) {
-            const float* s = halo + (ly + ty + i) * SW + lx;
-            float w[WWV];
-#pragma unroll
-            for (int k = 0; k < WWV; k += VW) {
-                if (VW == 4) {
-                    const float4 v = *reinterpret_cast<const float4*>(s + k);
-                    w[k] = v.x; w[k + 1] = v.y; w[k + 2] = v.z; w[k + 3] = v.w;
-                } else if (VW == 2) {
-                    const float2 v = *reinterpret_cast<const float2*>(s + k);
-                    w[k] = v.x; w[k + 1] = v.y;
-                } else {
-                    w[k] = s[k];
-                }
+            for (int q = 0; q < FWP; q += 4) {
+                const float4 t = *reinterpret_cast<const float4*>(taps + i * FWP + q);
+                f[q] = t.x; f[q + 1] = t.y; f[q + 2] = t.z; f[q + 3] = t.w;
             }
 #pragma unroll
-            for (int j = 0; j < FW; ++j)
+            for (int ty = 0; ty < TY; ++ty) {
+                const float* s = halo + (ly + ty + i) * SW + lx;
+                float w[WWV];
 #pragma unroll
-                for (int tx = 0; tx < TX; ++tx) acc[ty][tx] = fmaf(w[tx + j], f[j], acc[ty][tx]);
-        }
-    }
-
-    const int gx = gx0 + lx, gy = gy0 + ly;
-#pragma unroll
-    for (int ty = 0; ty < TY; ++ty) {
-        const int y = gy + ty;
-        if (y < pr.out_h) {
-            float* __restrict__ orow = pr.out + (ct_i64)y * pr.out_pitch + gx;
-            if (TX % 4 == 0) {
-#pragma unroll
-                for (int k = 0; k < TX; k += 4) {
-                    if (gx + k + 3 < pr.out_w) {
-                        *reinterpret_cast<float4*>(orow + k) =
-                            make_float4(acc[ty][k], acc[ty][k + 1], acc[ty][k + 2], acc[ty][k + 3]);
+                for (int k = 0; k < WWV; k += VW) {
+                    if (VW == 4) {
+                        const float4 v = *reinterpret_cast<const float4*>(s + k);
+                        w[k] = v.x; w[k + 1] = v.y; w[k + 2] = v.z; w[k + 3] = v.w;
+                    } else if (VW == 2) {
+                        const float2 v = *reinterpret_cast<const float2*>(s + k);
+                        w[k] = v.x; w[k + 1] = v.y;
                     } else {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (gx + k + e < pr.out_w) orow[k + e] = acc[ty][k + e];
+                        w[k] = s[k];
                     }
                 }
-            } else {
 #pragma unroll
-                for (int tx = 0; tx < TX; ++tx)
-                    if (gx + tx < pr.out_w) orow[tx] = acc[ty][tx];
+                for (int j = 0; j < FW; ++j)
+#pragma unroll
+                    for (int tx = 0; tx < TX; ++tx) acc[ty][tx] = fmaf(w[tx + j], f[j], acc[ty][tx]);
+            }
+        }
+
+        const int gx = gx0 + lx, gy = gy0 + ly;
+#pragma unroll
+        for (int ty = 0; ty < TY; ++ty) {
+            const int y = gy + ty;
+            if (y < pr.out_h) {
+                float* __restrict__ orow = pr.out + (ct_i64)y * pr.out_pitch + gx;
+                if (TX % 4 == 0) {
+#pragma unroll
+                    for (int k = 0; k < TX; k += 4) {
+                        if (gx + k + 3 < pr.out_w) {
+                            *reinterpret_cast<float4*>(orow + k) =
+                                make_float4(acc[ty][k], acc[ty][k + 1], acc[ty][k + 2], acc[ty][k + 3]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (gx + k + e < pr.out_w) orow[k + e] = acc[ty][k + e];
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int tx = 0; tx < TX; ++tx)
+                        if (gx + tx < pr.out_w) orow[tx] = acc[ty][tx];
+                }
             }
         }
     }
-    __syncthreads();   // the next item re-stages shared memory
+};
+
+#define CT_TILE(b) CtTile<CT_B##b##_BX, CT_B##b##_TX, CT_B##b##_TY, CT_B##b##_FW, CT_B##b##_FH>
+
+__device__ __forceinline__ void ct_stage_item(const CtBatchProblem& pr, const float* filters, int tile, float* buf)
+{
+    switch (pr.bucket) {
+#if CT_NB > 0
+    case 0: CT_TILE(0)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 1
+    case 1: CT_TILE(1)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 2
+    case 2: CT_TILE(2)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 3
+    case 3: CT_TILE(3)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 4
+    case 4: CT_TILE(4)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 5
+    case 5: CT_TILE(5)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 6
+    case 6: CT_TILE(6)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 7
+    case 7: CT_TILE(7)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 8
+    case 8: CT_TILE(8)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 9
+    case 9: CT_TILE(9)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 10
+    case 10: CT_TILE(10)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 11
+    case 11: CT_TILE(11)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 12
+    case 12: CT_TILE(12)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 13
+    case 13: CT_TILE(13)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 14
+    case 14: CT_TILE(14)::stage(pr, filters, tile, buf); break;
+#endif
+#if CT_NB > 15
+    case 15: CT_TILE(15)::stage(pr, filters, tile, buf); break;
+#endif
+    default: break;
+    }
 }
 
-#define CT_BUCKET_CASE(b)                                                                                  \
-    case b:                                                                                                \
-        ct_batch_tile<CT_B##b##_BX, CT_B##b##_TX, CT_B##b##_TY, CT_B##b##_FW, CT_B##b##_FH>(pr, p.filters, \
-                                                                                           it.y, sm);     \
-        break;
+__device__ __forceinline__ void ct_compute_item(const CtBatchProblem& pr, int tile, const float* buf)
+{
+    switch (pr.bucket) {
+#if CT_NB > 0
+    case 0: CT_TILE(0)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 1
+    case 1: CT_TILE(1)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 2
+    case 2: CT_TILE(2)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 3
+    case 3: CT_TILE(3)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 4
+    case 4: CT_TILE(4)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 5
+    case 5: CT_TILE(5)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 6
+    case 6: CT_TILE(6)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 7
+    case 7: CT_TILE(7)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 8
+    case 8: CT_TILE(8)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 9
+    case 9: CT_TILE(9)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 10
+    case 10: CT_TILE(10)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 11
+    case 11: CT_TILE(11)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 12
+    case 12: CT_TILE(12)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 13
+    case 13: CT_TILE(13)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 14
+    case 14: CT_TILE(14)::compute(pr, tile, buf); break;
+#endif
+#if CT_NB > 15
+    case 15: CT_TILE(15)::compute(pr, tile, buf); break;
+#endif
+    default: break;
+    }
+}
 
+// Persistent loop, two shared buffers: while item k is computed from one, the
+// copies of item k+1 into the other are in flight.
 extern "C" __global__ void __launch_bounds__(CT_NT) ct_corr2d_batch(const __grid_constant__ CtBatchParams p)
 {
     extern __shared__ float4 ct_smem4[];
-    float* sm = reinterpret_cast<float*>(ct_smem4);
-    __shared__ int s_w;
-    for (;;) {
-        if (threadIdx.x == 0) s_w = (int)atomicAdd(p.counter, 1u);
-        __syncthreads();
-        const int w = s_w;
+    float* const sm0 = reinterpret_cast<float*>(ct_smem4);
+    float* const sm1 = sm0 + CT_BUF_FLOATS;
+    __shared__ int s_w[2];
+    const int tid = threadIdx.x;
+    if (tid == 0) s_w[0] = (int)atomicAdd(p.counter, 1u);
+    __syncthreads();
+    {
+        const int w0 = s_w[0];
+        if (w0 < p.n_work) {
+            const uint2 it = p.work[w0];
+            ct_stage_item(p.probs[it.x], p.filters, (int)it.y, sm0);
+        }
+        ct_cp_commit();
+    }
+    for (int k = 0;; ++k) {
+        const int cur = k & 1;
+        float* const bcur = cur ? sm1 : sm0;
+        float* const bnxt = cur ? sm0 : sm1;
+        if (tid == 0) s_w[cur ^ 1] = (int)atomicAdd(p.counter, 1u);
+        __syncthreads();   // next index visible; every thread is done with bnxt
+        const int w = s_w[cur];
+        const int wn = s_w[cur ^ 1];
+        if (wn < p.n_work) {
+            const uint2 it = p.work[wn];
+            ct_stage_item(p.probs[it.x], p.filters, (int)it.y, bnxt);
+        }
+        ct_cp_commit();
+        ct_cp_wait<1>();   // this thread's copies of item w have landed
+        __syncthreads();   // ... and every other thread's
         if (w >= p.n_work) break;
         const uint2 it = p.work[w];
-        const CtBatchProblem pr = p.probs[it.x];
-        switch (pr.bucket) {
-#if CT_NB > 0
-            CT_BUCKET_CASE(0)
-#endif
-#if CT_NB > 1
-            CT_BUCKET_CASE(1)
-#endif
-#if CT_NB > 2
-            CT_BUCKET_CASE(2)
-#endif
-#if CT_NB > 3
-            CT_BUCKET_CASE(3)
-#endif
-#if CT_NB > 4
-            CT_BUCKET_CASE(4)
-#endif
-#if CT_NB > 5
-            CT_BUCKET_CASE(5)
-#endif
-#if CT_NB > 6
-            CT_BUCKET_CASE(6)
-#endif
-#if CT_NB > 7
-            CT_BUCKET_CASE(7)
-#endif
-#if CT_NB > 8
-            CT_BUCKET_CASE(8)
-#endif
-#if CT_NB > 9
-            CT_BUCKET_CASE(9)
-#endif
-#if CT_NB > 10
-            CT_BUCKET_CASE(10)
-#endif
-#if CT_NB > 11
-            CT_BUCKET_CASE(11)
-#endif
-#if CT_NB > 12
-            CT_BUCKET_CASE(12)
-#endif
-#if CT_NB > 13
-            CT_BUCKET_CASE(13)
-#endif
-#if CT_NB > 14
-            CT_BUCKET_CASE(14)
-#endif
-#if CT_NB > 15
-            CT_BUCKET_CASE(15)
-#endif
-            default: __syncthreads(); break;
-        }
+        ct_compute_item(p.probs[it.x], (int)it.y, bcur);
     }
+    ct_cp_wait<0>();
 }
