@@ -128,34 +128,41 @@ struct CtTile {
 #pragma unroll
             for (int tx = 0; tx < TX; ++tx) acc[ty][tx] = 0.0f;
 
+        // Input rows slide through a register window once each; row r feeds
+        // every output row ty with filter row i = r - ty, whose taps are read
+        // as broadcast 16-byte loads.  Per output the taps are still added in
+        // (i, j) order.
 #pragma unroll 1
-        for (int i = 0; i < FH; ++i) {
-            float f[FWP];
+        for (int r = 0; r < TY + FH - 1; ++r) {
+            const float* s = halo + (ly + r) * SW + lx;
+            float w[WWV];
 #pragma unroll
-            for (int q = 0; q < FWP; q += 4) {
-                const float4 t = *reinterpret_cast<const float4*>(taps + i * FWP + q);
-                f[q] = t.x; f[q + 1] = t.y; f[q + 2] = t.z; f[q + 3] = t.w;
+            for (int k = 0; k < WWV; k += VW) {
+                if (VW == 4) {
+                    const float4 v = *reinterpret_cast<const float4*>(s + k);
+                    w[k] = v.x; w[k + 1] = v.y; w[k + 2] = v.z; w[k + 3] = v.w;
+                } else if (VW == 2) {
+                    const float2 v = *reinterpret_cast<const float2*>(s + k);
+                    w[k] = v.x; w[k + 1] = v.y;
+                } else {
+                    w[k] = s[k];
+                }
             }
 #pragma unroll
             for (int ty = 0; ty < TY; ++ty) {
-                const float* s = halo + (ly + ty + i) * SW + lx;
-                float w[WWV];
+                const int i = r - ty;
+                if (i >= 0 && i < FH) {
+                    float f[FWP];
 #pragma unroll
-                for (int k = 0; k < WWV; k += VW) {
-                    if (VW == 4) {
-                        const float4 v = *reinterpret_cast<const float4*>(s + k);
-                        w[k] = v.x; w[k + 1] = v.y; w[k + 2] = v.z; w[k + 3] = v.w;
-                    } else if (VW == 2) {
-                        const float2 v = *reinterpret_cast<const float2*>(s + k);
-                        w[k] = v.x; w[k + 1] = v.y;
-                    } else {
-                        w[k] = s[k];
+                    for (int q = 0; q < FWP; q += 4) {
+                        const float4 t = *reinterpret_cast<const float4*>(taps + i * FWP + q);
+                        f[q] = t.x; f[q + 1] = t.y; f[q + 2] = t.z; f[q + 3] = t.w;
                     }
+#pragma unroll
+                    for (int j = 0; j < FW; ++j)
+#pragma unroll
+                        for (int tx = 0; tx < TX; ++tx) acc[ty][tx] = fmaf(w[tx + j], f[j], acc[ty][tx]);
                 }
-#pragma unroll
-                for (int j = 0; j < FW; ++j)
-#pragma unroll
-                    for (int tx = 0; tx < TX; ++tx) acc[ty][tx] = fmaf(w[tx + j], f[j], acc[ty][tx]);
             }
         }
 
