@@ -310,11 +310,13 @@ def run_ours(args):
                 torch.distributed.barrier()
             torch.cuda.synchronize()
             t_wall = time.time()
+            torch.cuda.nvtx.range_push("timed")
             for i in range(k):
                 flush.fill_(i & 0xFF)
                 ev[i][0].record(stream)
                 ct.conv2d_raw(p, cfg, d_img.data_ptr(), hf, d_out.data_ptr(), stream.cuda_stream)
                 ev[i][1].record(stream)
+            torch.cuda.nvtx.range_pop()
             stream.synchronize()
             torch.cuda.synchronize()
             if world > 1:
@@ -471,7 +473,7 @@ def run_batch(args):
     def batch_step():
         batch.run(stream)
 
-    def timed(step, k, w):
+    def timed(step, k, w, name):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         with torch.cuda.stream(stream):
             for _ in range(w):
@@ -479,11 +481,13 @@ def run_batch(args):
             stream.synchronize()
             if world > 1:
                 torch.distributed.barrier()
+            torch.cuda.nvtx.range_push(name)
             for i in range(k):
                 flush.fill_(i & 0xFF)
                 ev[i][0].record(stream)
                 step()
                 ev[i][1].record(stream)
+            torch.cuda.nvtx.range_pop()
             stream.synchronize()
             if world > 1:
                 torch.distributed.barrier()
@@ -493,9 +497,9 @@ def run_batch(args):
     clocks = ClockSampler(local)
     clocks.start()
     tb0 = time.time()
-    ms_batch = timed(batch_step, k, max(3, args.warmup))
+    ms_batch = timed(batch_step, k, max(3, args.warmup), "batch_timed")
     tb1 = time.time()
-    ms_plain = timed(plain_step, k, max(3, args.warmup)) if plain_args else [float("nan")]
+    ms_plain = timed(plain_step, k, max(3, args.warmup), "plain_timed") if plain_args else [float("nan")]
     clocks.stop()
     # the batched outputs equal the per-problem outputs bit for bit
     batch_step()
