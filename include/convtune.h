@@ -298,6 +298,8 @@ typedef struct {
 
 typedef struct {
     int32_t block_x, block_y, tile_x, tile_y;
+    int32_t unroll;          /* 1: the input-row loop is unrolled */
+    int32_t reserved;
 } ct_bucket_config;
 
 typedef struct {

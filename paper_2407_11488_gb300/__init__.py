@@ -93,7 +93,8 @@ class BatchItem(ctypes.Structure):
 
 
 class BucketConfig(ctypes.Structure):
-    _fields_ = [("block_x", i32), ("block_y", i32), ("tile_x", i32), ("tile_y", i32)]
+    _fields_ = [("block_x", i32), ("block_y", i32), ("tile_x", i32), ("tile_y", i32), ("unroll", i32),
+                ("reserved", i32)]
 
 
 class BatchOpts(ctypes.Structure):
@@ -493,7 +494,7 @@ class Batch:
             _check(_load().ct_batch_bucket(self.handle, k, ctypes.byref(fw), ctypes.byref(fh), ctypes.byref(n),
                                            ctypes.byref(c), ctypes.byref(pp)))
             res.append({"filter": (fw.value, fh.value), "n_items": n.value, "pp": pp.value,
-                        "config": {f: getattr(c, f) for f, _ in BucketConfig._fields_}})
+                        "config": {f: getattr(c, f) for f, _ in BucketConfig._fields_ if f != "reserved"}})
         return res
 
     def item_bucket(self, i: int) -> int:

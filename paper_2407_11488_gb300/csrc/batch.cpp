@@ -17,7 +17,7 @@ static const char kBatchSource[] =
 namespace {
 
 struct TileCfg {
-    int bx = 32, tx = 4, ty = 4;
+    int bx = 32, tx = 4, ty = 4, un = 0;
 };
 
 // Mirrors of the device structs in batch.cuh.
@@ -41,6 +41,9 @@ static_assert(sizeof(DevParams) == 40, "DevParams layout");
 struct WorkItem {
     uint32_t problem, tile;
 };
+
+constexpr int64_t kSmemPerSM = 233472;   // shared memory per SM usable by blocks
+constexpr int kMinBlocks = 4;            // resident blocks per SM the batch kernel is built for
 
 struct BucketDesc {
     int fw, fh;
@@ -71,6 +74,7 @@ std::vector<std::string> batch_options(int threads, int dtype, const std::vector
     def("CT_NT", threads);
     def("CT_DTYPE", dtype);
     def("CT_NB", (int)b.size());
+    def("CT_MINB", kMinBlocks);
     int64_t buf = 4;
     for (const auto& d : b) buf = std::max(buf, bucket_buf_floats(threads, d.cfg, d.fw, d.fh));
     def("CT_BUF_FLOATS", (int)buf);
@@ -81,6 +85,7 @@ std::vector<std::string> batch_options(int threads, int dtype, const std::vector
         def(p + "TY", b[k].cfg.ty);
         def(p + "FW", b[k].fw);
         def(p + "FH", b[k].fh);
+        def(p + "UN", b[k].cfg.un);
     }
     add_env_options(o);
     return o;
@@ -207,19 +212,26 @@ DevProblem dev_problem(const ct_batch& B, int i, int bucket, const TileCfg& c)
     return d;
 }
 
-std::vector<TileCfg> bucket_candidates(int threads, int fw, int fh, int smem_limit)
+// Candidate tiles of one bucket: block width, register tile, row-loop
+// unrolling; the two item buffers must leave room for min_blocks blocks per
+// SM, and a fully unrolled body stays below ~6k FMAs (instruction cache).
+std::vector<TileCfg> bucket_candidates(int threads, int fw, int fh, int smem_limit, int min_blocks)
 {
     std::vector<TileCfg> out;
-    for (int bx : {16, 32, 64, 128}) {
+    const int64_t cap = std::min<int64_t>(smem_limit, (int64_t)kSmemPerSM / std::max(1, min_blocks) - 1024);
+    for (int bx : {16, 32, 64}) {
         if (bx > threads || threads % bx) continue;
-        for (int tx : {1, 2, 4})
-            for (int ty : {1, 2, 4, 8}) {
-                TileCfg c{bx, tx, ty};
-                if ((bx * tx) % 4) continue;
-                if (bucket_smem(threads, c, fw, fh) > smem_limit) continue;
-                out.push_back(c);
-            }
+        for (int tx : {2, 4})
+            for (int ty : {1, 2, 4, 8})
+                for (int un : {0, 1}) {
+                    TileCfg c{bx, tx, ty, un};
+                    if ((bx * tx) % 4) continue;
+                    if (bucket_smem(threads, c, fw, fh) > cap) continue;
+                    if (un && (int64_t)tx * ty * fw * (fh + ty - 1) > 6144) continue;
+                    out.push_back(c);
+                }
     }
+    if (out.empty()) out.push_back(TileCfg{std::min(32, threads), 4, 1, 0});
     return out;
 }
 
@@ -228,7 +240,7 @@ std::vector<TileCfg> bucket_candidates(int threads, int fw, int fh, int smem_lim
 ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o, CompilePool& pool,
                       cudaStream_t s, int smem_limit)
 {
-    std::vector<TileCfg> cand = bucket_candidates(B.threads, bk.fw, bk.fh, smem_limit);
+    std::vector<TileCfg> cand = bucket_candidates(B.threads, bk.fw, bk.fh, smem_limit, kMinBlocks);
     if (cand.empty()) return fail(CT_ERR_INVALID_CONFIG, "no tile fits shared memory for filter %dx%d", bk.fw, bk.fh);
     // sample of problems: sorted by size, evenly spaced, always the extremes
     std::vector<int> its = bk.items;
@@ -458,7 +470,7 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
             if (o.tune) {
                 if ((st = tune_bucket(*B, bk, o, pool, s, smem_limit)) != CT_OK) return st;
             } else {
-                bk.cfg = TileCfg{32, 4, 4};
+                bk.cfg = TileCfg{32, 4, 4, 0};
                 if (threads % 32) bk.cfg.bx = 16;
                 while (bucket_smem(threads, bk.cfg, bk.fw, bk.fh) > smem_limit && bk.cfg.ty > 1) bk.cfg.ty /= 2;
             }
@@ -561,7 +573,7 @@ CT_API ct_status ct_batch_bucket(const ct_batch* b, int32_t k, int32_t* filter_w
     if (filter_w) *filter_w = bk.fw;
     if (filter_h) *filter_h = bk.fh;
     if (n_items) *n_items = (int32_t)bk.items.size();
-    if (cfg) *cfg = ct_bucket_config{bk.cfg.bx, b->threads / bk.cfg.bx, bk.cfg.tx, bk.cfg.ty};
+    if (cfg) *cfg = ct_bucket_config{bk.cfg.bx, b->threads / bk.cfg.bx, bk.cfg.tx, bk.cfg.ty, bk.cfg.un, 0};
     if (pp) *pp = bk.pp;
     return CT_OK;
 }

@@ -17,6 +17,8 @@
 // Macros: CT_NT (threads per block), CT_DTYPE (0 FP32, 1 BF16 image),
 // CT_NB (buckets), and for every bucket b < CT_NB: CT_B<b>_BX (block width;
 // block height = CT_NT / BX), CT_B<b>_TX, CT_B<b>_TY (register tile),
+// CT_B<b>_UN (1: input-row loop unrolled), CT_MINB (blocks per SM the
+// register allocation must allow),
 // CT_B<b>_FW, CT_B<b>_FH (filter); CT_BUF_FLOATS, the size of one item
 // buffer (the largest bucket's, a multiple of 4 floats).
 //
@@ -71,7 +73,7 @@ __device__ __forceinline__ void ct_cp_wait()
 // stage() and compute() are real calls, not inlined: each bucket's routine
 // then gets its own register allocation and the kernel needs only the
 // largest of them, instead of the union a single inlined body would hold.
-template <int BX, int TX, int TY, int FW, int FH>
+template <int BX, int TX, int TY, int FW, int FH, int UN>
 struct CtTile {
     static constexpr int BY = CT_NT / BX;
     static constexpr int TW = BX * TX, TH = BY * TY;
@@ -114,6 +116,41 @@ struct CtTile {
         }
     }
 
+    static __device__ __forceinline__ void row_step(const float* halo, const float* taps, int lx, int ly, int r,
+                                                    float (&acc)[TY][TX])
+    {
+        const float* s = halo + (ly + r) * SW + lx;
+        float w[WWV];
+#pragma unroll
+        for (int k = 0; k < WWV; k += VW) {
+            if (VW == 4) {
+                const float4 v = *reinterpret_cast<const float4*>(s + k);
+                w[k] = v.x; w[k + 1] = v.y; w[k + 2] = v.z; w[k + 3] = v.w;
+            } else if (VW == 2) {
+                const float2 v = *reinterpret_cast<const float2*>(s + k);
+                w[k] = v.x; w[k + 1] = v.y;
+            } else {
+                w[k] = s[k];
+            }
+        }
+#pragma unroll
+        for (int ty = 0; ty < TY; ++ty) {
+            const int i = r - ty;
+            if (i >= 0 && i < FH) {
+                float f[FWP];
+#pragma unroll
+                for (int q = 0; q < FWP; q += 4) {
+                    const float4 t = *reinterpret_cast<const float4*>(taps + i * FWP + q);
+                    f[q] = t.x; f[q + 1] = t.y; f[q + 2] = t.z; f[q + 3] = t.w;
+                }
+#pragma unroll
+                for (int j = 0; j < FW; ++j)
+#pragma unroll
+                    for (int tx = 0; tx < TX; ++tx) acc[ty][tx] = fmaf(w[tx + j], f[j], acc[ty][tx]);
+            }
+        }
+    }
+
     // Computes and stores one item whose taps and halo are in buf.
     static __device__ __noinline__ void compute(const CtBatchProblem& pr, int tile, const float* buf)
     {
@@ -130,40 +167,15 @@ struct CtTile {
 
         // Input rows slide through a register window once each; row r feeds
         // every output row ty with filter row i = r - ty, whose taps are read
-        // as broadcast 16-byte loads.  Per output the taps are still added in
-        // (i, j) order.
+        // as broadcast 16-byte loads.  UN = 1 unrolls the row loop (constant
+        // offsets, no per-row predicates); UN = 0 keeps it rolled.  Per output
+        // the taps are added in (i, j) order either way.
+        if constexpr (UN != 0) {
+#pragma unroll
+            for (int r = 0; r < TY + FH - 1; ++r) row_step(halo, taps, lx, ly, r, acc);
+        } else {
 #pragma unroll 1
-        for (int r = 0; r < TY + FH - 1; ++r) {
-            const float* s = halo + (ly + r) * SW + lx;
-            float w[WWV];
-#pragma unroll
-            for (int k = 0; k < WWV; k += VW) {
-                if (VW == 4) {
-                    const float4 v = *reinterpret_cast<const float4*>(s + k);
-                    w[k] = v.x; w[k + 1] = v.y; w[k + 2] = v.z; w[k + 3] = v.w;
-                } else if (VW == 2) {
-                    const float2 v = *reinterpret_cast<const float2*>(s + k);
-                    w[k] = v.x; w[k + 1] = v.y;
-                } else {
-                    w[k] = s[k];
-                }
-            }
-#pragma unroll
-            for (int ty = 0; ty < TY; ++ty) {
-                const int i = r - ty;
-                if (i >= 0 && i < FH) {
-                    float f[FWP];
-#pragma unroll
-                    for (int q = 0; q < FWP; q += 4) {
-                        const float4 t = *reinterpret_cast<const float4*>(taps + i * FWP + q);
-                        f[q] = t.x; f[q + 1] = t.y; f[q + 2] = t.z; f[q + 3] = t.w;
-                    }
-#pragma unroll
-                    for (int j = 0; j < FW; ++j)
-#pragma unroll
-                        for (int tx = 0; tx < TX; ++tx) acc[ty][tx] = fmaf(w[tx + j], f[j], acc[ty][tx]);
-                }
-            }
+            for (int r = 0; r < TY + FH - 1; ++r) row_step(halo, taps, lx, ly, r, acc);
         }
 
         const int gx = gx0 + lx, gy = gy0 + ly;
@@ -194,7 +206,7 @@ struct CtTile {
     }
 };
 
-#define CT_TILE(b) CtTile<CT_B##b##_BX, CT_B##b##_TX, CT_B##b##_TY, CT_B##b##_FW, CT_B##b##_FH>
+#define CT_TILE(b) CtTile<CT_B##b##_BX, CT_B##b##_TX, CT_B##b##_TY, CT_B##b##_FW, CT_B##b##_FH, CT_B##b##_UN>
 
 __device__ __forceinline__ void ct_stage_item(const CtBatchProblem& pr, const float* filters, int tile, float* buf)
 {
@@ -308,7 +320,10 @@ __device__ __forceinline__ void ct_compute_item(const CtBatchProblem& pr, int ti
 
 // Persistent loop, two shared buffers: while item k is computed from one, the
 // copies of item k+1 into the other are in flight.
-extern "C" __global__ void __launch_bounds__(CT_NT) ct_corr2d_batch(const __grid_constant__ CtBatchParams p)
+#ifndef CT_MINB
+#define CT_MINB 1
+#endif
+extern "C" __global__ void __launch_bounds__(CT_NT, CT_MINB) ct_corr2d_batch(const __grid_constant__ CtBatchParams p)
 {
     extern __shared__ float4 ct_smem4[];
     float* const sm0 = reinterpret_cast<float*>(ct_smem4);
