@@ -271,21 +271,9 @@ ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o,
         keys.push_back(key);
         futs.push_back(pool.request(key, [thr, dt, one, dir] { return compile_batch(thr, dt, one, dir); }));
     }
-    // Each candidate is measured on each sampled problem with the problem's
-    // tile list repeated until it covers several waves of the persistent
-    // grid: the combined launch keeps the GPU full with other problems, so the
-    // steady-state cost per tile, not an idle GPU's latency, is what counts.
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t target_tiles = (int64_t)8 * kMinBlocks * sms;
-    auto repeats_for = [&](int64_t nt) { return nt > 0 ? std::max<int64_t>(1, (target_tiles + nt - 1) / nt) : 1; };
     int64_t max_tiles = 1;
     for (const auto& c : cand)
-        for (int i : sample) {
-            const int64_t nt = tiles_of(B.items[(size_t)i], B.threads, c);
-            max_tiles = std::max(max_tiles, nt * repeats_for(nt));
-        }
+        for (int i : sample) max_tiles = std::max(max_tiles, tiles_of(B.items[(size_t)i], B.threads, c));
     void* d_prob = nullptr;
     void* d_work = nullptr;
     unsigned* d_cnt = nullptr;
@@ -317,11 +305,9 @@ ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o,
         for (size_t ii = 0; ii < ni; ++ii) {
             const int item = sample[ii];
             const DevProblem dp = dev_problem(B, item, 0, cand[ci]);
-            const int64_t nt1 = tiles_of(B.items[(size_t)item], B.threads, cand[ci]);
-            const int64_t reps = repeats_for(nt1);
-            const int64_t nt = nt1 * reps;
+            const int64_t nt = tiles_of(B.items[(size_t)item], B.threads, cand[ci]);
             work.resize((size_t)nt);
-            for (int64_t k = 0; k < nt; ++k) work[(size_t)k] = WorkItem{0u, (uint32_t)(k % nt1)};
+            for (int64_t k = 0; k < nt; ++k) work[(size_t)k] = WorkItem{0u, (uint32_t)k};
             cudaMemcpyAsync(d_prob, &dp, sizeof dp, cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(d_work, work.data(), (size_t)nt * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
             ct_status st = load_variant(*v);
@@ -348,7 +334,7 @@ ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o,
                 continue;
             }
             std::sort(ms.begin(), ms.end());
-            t[ci * ni + ii] = ms[ms.size() / 2] / (double)reps;
+            t[ci * ni + ii] = ms[ms.size() / 2];
         }
         unload_variant(*v);
     }
