@@ -484,7 +484,7 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
     compile_cpu += B->module->compile_ms;
     if (B->module->status != CT_OK) return fail(CT_ERR_COMPILE, "%s", B->module->error.c_str());
     if (B->module->smem > smem_limit) return fail(CT_ERR_INVALID_CONFIG, "batch kernel needs too much shared memory");
-    if ((st = load_variant(*B->module)) != CT_OK) return st;
+    if ((st = load_variant(*B->module)) != CT_OK) return st;   // also fills in the register count
     // problem table and work list: most expensive tiles first
     std::vector<DevProblem> probs;
     for (int i = 0; i < n; ++i) {

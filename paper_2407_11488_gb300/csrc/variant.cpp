@@ -327,6 +327,11 @@ ct_status load_variant(Variant& v)
         }
         e = cudaLibraryGetKernel(&v.kern, v.lib, v.kname.c_str());
         if (e != cudaSuccess) return cuda_fail(e, "cudaLibraryGetKernel");
+        if (v.regs == 0) {   // no ptxas report (e.g. a compile NVRTC served itself): ask the driver
+            cudaFuncAttributes fa;
+            if (cudaFuncGetAttributes(&fa, (const void*)v.kern) == cudaSuccess) v.regs = fa.numRegs;
+            else cudaGetLastError();
+        }
     }
     if (v.loaded_device != dev || v.smem_attr != v.smem) {
         e = cudaFuncSetAttribute((const void*)v.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
