@@ -343,6 +343,83 @@ CT_API ct_status ct_batch_bucket(const ct_batch* b, int32_t k, int32_t* filter_w
 CT_API int32_t ct_batch_item_bucket(const ct_batch* b, int32_t i);
 CT_API void ct_batch_free(ct_batch* b);
 
+/* ---- serving: continuous batching under a device-memory budget ------------
+ *
+ * A server owns a device-memory budget (one arena) and a dispatcher thread.
+ * Each submitted request is admitted, in arrival order, as soon as its image
+ * and output fit the budget; its image is copied in; once the copy has landed
+ * it joins the next launch of the persistent batch kernel (see ct_batch_*).
+ * Up to max_launches launches run at once on separate streams, so requests
+ * arriving while others are on the GPU are admitted and launched as memory
+ * and launch slots free up, and their work overlaps with the running work.
+ * A launch starts at once when none of the server's launches is running,
+ * otherwise when max_batch requests are ready or the oldest ready request has
+ * waited max_wait_us.  Each square filter size of [filter_min, filter_max]
+ * (same parity as filter_min) has one resident tile configuration, tuned at
+ * creation when opts->tune is set, so a result does not depend on which
+ * requests shared its launch.  All waits are host-side and bounded by the
+ * caller's timeout; no device code waits. */
+
+typedef struct {
+    int64_t mem_budget_bytes; /* device memory for images, outputs and launch tables */
+    int32_t dtype;            /* ct_dtype of all images */
+    int32_t max_batch;        /* requests per launch (0: 64) */
+    int32_t max_launches;     /* launches in flight at once (0: 3) */
+    int32_t max_wait_us;      /* batching delay while other launches run (0: 200) */
+    int32_t tune;             /* 1: tune each filter size's tile at creation */
+    int32_t filter_min, filter_max;  /* served square filter sizes (0: 3 and 17) */
+    int32_t reserved;
+    int64_t staging_bytes;    /* pinned host staging per launch slot for the tables (0: 16 MiB) */
+} ct_server_opts;
+
+typedef struct {
+    const void* h_image;   /* in_h x in_pitch host elements (pinned for asynchronous copies), read after
+                              admission and until the request completes; or NULL with image_id */
+    uint64_t image_id;     /* a resident image (ct_server_image_register), 0 for none */
+    float* h_out;          /* out_h x out_pitch host floats (pinned), written when the request completes */
+    const void* h_filter;  /* filter_h x filter_w (float or bf16 bits), copied at submit */
+    int32_t out_w, out_h, filter_w, filter_h;
+    int64_t in_pitch, out_pitch;   /* elements; rows of 16-byte multiples */
+} ct_request;
+
+typedef struct {
+    int64_t submitted, completed, failed, launches;
+    double mean_batch;     /* requests per launch */
+    double p50_ms, p99_ms, mean_ms, max_ms;   /* submit -> output on the host */
+    double wall_s;         /* first submit to last completion since the last reset */
+    double req_per_s, gflops;
+    int64_t peak_mem_bytes;
+} ct_server_stats;
+
+typedef struct ct_server ct_server;
+
+/* Creates a server on the current device: tunes (opts->tune) and compiles the
+ * persistent kernel for the served filter sizes, allocates the budget and
+ * starts the dispatcher thread. */
+CT_API ct_status ct_server_create(const ct_server_opts* opts, ct_server** out);
+/* Uploads an image that stays resident (counted in the budget) until
+ * released; requests can name it instead of carrying a host image.
+ * Synchronous.  CT_ERR_OOM when it does not fit the budget now. */
+CT_API ct_status ct_server_image_register(ct_server* s, const void* h_image, int32_t in_w, int32_t in_h,
+                                          int64_t in_pitch, uint64_t* image_id);
+CT_API ct_status ct_server_image_release(ct_server* s, uint64_t image_id);
+/* Queues one request; returns at once with its id.  CT_ERR_UNSUPPORTED for a
+ * filter size the server does not serve, CT_ERR_OOM for a request larger
+ * than the whole budget.  Every request must be collected with
+ * ct_server_wait. */
+CT_API ct_status ct_server_submit(ct_server* s, const ct_request* rq, uint64_t* request_id);
+/* Waits up to timeout_us (< 0: no limit) for the request; on success h_out
+ * holds the result and *latency_ms the time from submit to completion.
+ * CT_ERR_TIMEOUT when it is not done in time (the request stays queued and
+ * can be waited again). */
+CT_API ct_status ct_server_wait(ct_server* s, uint64_t request_id, int64_t timeout_us, double* latency_ms);
+/* Waits until nothing is queued or running (timeout as above). */
+CT_API ct_status ct_server_drain(ct_server* s, int64_t timeout_us);
+CT_API ct_status ct_server_stats_get(ct_server* s, ct_server_stats* out);
+CT_API ct_status ct_server_stats_reset(ct_server* s);
+/* Stops the dispatcher after the queued work finishes and frees everything. */
+CT_API void ct_server_destroy(ct_server* s);
+
 /* ---- batched correlation without allocation ------------------------------
  *
  * The paper has no counterpart to this entry point.  It serves callers that

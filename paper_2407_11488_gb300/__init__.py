@@ -107,6 +107,23 @@ class BatchInfo(ctypes.Structure):
                 ("smem_bytes", i32), ("regs", i32), ("plan_ms", dbl), ("tune_ms", dbl), ("compile_cpu_ms", dbl)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", i64), ("dtype", i32), ("max_batch", i32), ("max_launches", i32),
+                ("max_wait_us", i32), ("tune", i32), ("filter_min", i32), ("filter_max", i32), ("reserved", i32),
+                ("staging_bytes", i64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("h_image", vp), ("image_id", u64), ("h_out", vp), ("h_filter", vp), ("out_w", i32),
+                ("out_h", i32), ("filter_w", i32), ("filter_h", i32), ("in_pitch", i64), ("out_pitch", i64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", i64), ("completed", i64), ("failed", i64), ("launches", i64), ("mean_batch", dbl),
+                ("p50_ms", dbl), ("p99_ms", dbl), ("mean_ms", dbl), ("max_ms", dbl), ("wall_s", dbl),
+                ("req_per_s", dbl), ("gflops", dbl), ("peak_mem_bytes", i64)]
+
+
 P = ctypes.POINTER
 _SIGS = {
     "ct_version": (cp, []),
@@ -138,6 +155,15 @@ _SIGS = {
     "ct_batch_item_bucket": (i32, [vp, i32]),
     "ct_batch_free": (None, [vp]),
     "ct_batch_run_noalloc": (i32, [P(BatchItem), i32, i32, vp]),
+    "ct_server_create": (i32, [P(ServerOpts), P(vp)]),
+    "ct_server_image_register": (i32, [vp, vp, i32, i32, i64, P(u64)]),
+    "ct_server_image_release": (i32, [vp, u64]),
+    "ct_server_submit": (i32, [vp, P(Request), P(u64)]),
+    "ct_server_wait": (i32, [vp, u64, i64, P(dbl)]),
+    "ct_server_drain": (i32, [vp, i64]),
+    "ct_server_stats_get": (i32, [vp, P(ServerStats)]),
+    "ct_server_stats_reset": (i32, [vp]),
+    "ct_server_destroy": (None, [vp]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -504,3 +530,70 @@ class Batch:
         if getattr(self, "handle", None) and _lib is not None:
             _lib.ct_batch_free(self.handle)
             self.handle = None
+
+
+# ------------------------------------------------------------------ serving ---
+class Server:
+    """Continuous-batching request server (ct_server_*).  Host buffers passed
+    to submit() are kept referenced until the request is waited."""
+
+    def __init__(self, mem_budget_bytes, *, dtype=CT_F32, max_batch=64, max_launches=3, max_wait_us=200,
+                 tune=True, filter_min=3, filter_max=17, staging_bytes=0):
+        o = ServerOpts(int(mem_budget_bytes), dtype, max_batch, max_launches, max_wait_us, int(tune), filter_min,
+                       filter_max, 0, int(staging_bytes))
+        h = vp()
+        _check(_load().ct_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h
+        self.dtype = dtype
+        self._refs = {}
+
+    def register_image(self, h_image, in_w=None) -> int:
+        """Uploads a host image tensor (in_h, in_pitch) that stays resident."""
+        iid = u64()
+        in_w = int(h_image.shape[1]) if in_w is None else in_w
+        _check(_load().ct_server_image_register(self.handle, ctypes.c_void_p(h_image.data_ptr()), in_w,
+                                                int(h_image.shape[0]), int(h_image.stride(0)), ctypes.byref(iid)))
+        return iid.value
+
+    def release_image(self, image_id: int):
+        _check(_load().ct_server_image_release(self.handle, image_id))
+
+    def submit(self, h_out, filt, out_w, out_h, *, h_image=None, image_id=0, in_pitch=None) -> int:
+        fb = _filter_bytes(filt, self.dtype)
+        fh, fw = fb.shape
+        if in_pitch is None:
+            in_pitch = int(h_image.stride(0)) if h_image is not None else 0
+        rq = Request(ctypes.c_void_p(h_image.data_ptr()) if h_image is not None else None, image_id,
+                     ctypes.c_void_p(h_out.data_ptr()), fb.ctypes.data_as(vp), out_w, out_h, fw, fh, in_pitch,
+                     int(h_out.stride(0)))
+        rid = u64()
+        _check(_load().ct_server_submit(self.handle, ctypes.byref(rq), ctypes.byref(rid)))
+        self._refs[rid.value] = (h_image, h_out, fb)
+        return rid.value
+
+    def wait(self, request_id: int, timeout_us: int = -1) -> float:
+        lat = dbl()
+        st = _load().ct_server_wait(self.handle, request_id, timeout_us, ctypes.byref(lat))
+        if st != -7:
+            self._refs.pop(request_id, None)
+        _check(st)
+        return lat.value
+
+    def drain(self, timeout_us: int = -1):
+        _check(_load().ct_server_drain(self.handle, timeout_us))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_load().ct_server_stats_get(self.handle, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def reset_stats(self):
+        _check(_load().ct_server_stats_reset(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ct_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()

@@ -266,3 +266,13 @@ def test_batch_validation_without_gpu(ctlib):
     if NO_GPU:
         items[0] = ctlib.BatchItem(16, 16, 16, 64, 64, 5, 5, 68, 64)
         assert ctlib.lib().ct_batch_create(items, 1, None, ctypes.byref(h)) == -8
+
+
+@pytest.mark.skipif(not NO_GPU, reason="checks the no-device path")
+def test_server_without_gpu(ctlib):
+    with pytest.raises(ctlib.CTError) as e:
+        ctlib.Server(1 << 20, tune=False)
+    assert e.value.status == -8
+    import ctypes
+    h = ctlib.vp()
+    assert ctlib.lib().ct_server_create(None, ctypes.byref(h)) == -1
