@@ -41,6 +41,8 @@ WORKLOADS = {
     "small": (256, 256, 5, 0, "small"),
 }
 BATCH = {"count": 64, "side_lo": 128, "side_hi": 4096, "filters": (3, 5, 7, 11, 17), "seed": 2}
+SERVE = {"rate": 2000.0, "side_lo": 64, "side_hi": 2048, "filters": (3, 5, 7, 9, 11, 13, 15, 17), "seed": 3,
+         "budget": 32 << 30}
 FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM per clock (4 partitions x 32)
 
 
@@ -50,7 +52,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch"], default="full")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch", "serve"], default="full")
+    ap.add_argument("--requests", type=int, default=100000, help="serve: requests of the Poisson stream")
+    ap.add_argument("--sat-requests", type=int, default=20000, help="serve: requests of the saturation runs")
     ap.add_argument("--anneal-chains", type=int, default=4)
     ap.add_argument("--batch-plain", choices=["tune", "skip"], default="tune",
                     help="skip: time only the batched path (profiling)")
@@ -561,12 +565,149 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Serving: a Poisson stream of correlation requests (open loop, 2000/s)
+    through the continuous-batching server for latency percentiles, then
+    closed-loop saturation of the server against the plain per-request path
+    (one ct_conv2d_host_pitched call per request, configuration tuned per
+    filter size) on the same requests."""
+    import queue
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2407_11488_gb300 import build as _build
+    _build.build()
+    import paper_2407_11488_gb300 as ct
+    import synthetic
+
+    ct.set_cache_dir(args.cache_dir or os.path.join(tempfile.gettempdir(), f"convtune-cache-{os.getuid()}"))
+    info = ct.device_query()
+    n = args.requests
+    shapes = synthetic.uneven_batch(SERVE["seed"], n, SERVE["side_lo"], SERVE["side_hi"], SERVE["filters"])
+    u = (synthetic.splitmix64(SERVE["seed"], 1 << 42, n) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    arrivals = np.cumsum(-np.log1p(-u) / SERVE["rate"])
+    fmax = max(SERVE["filters"])
+    smax = SERVE["side_hi"] + fmax - 1
+    big, _ = synthetic.make_problem(SERVE["seed"], SERVE["side_hi"], SERVE["side_hi"], fmax, fmax)
+    h_big = torch.from_numpy(big).pin_memory()
+    pool = {fs: [np.ascontiguousarray(synthetic.uniform_pm1(SERVE["seed"] * 7 + fs, k * fs * fs, fs * fs)
+                                      .reshape(fs, fs)) for k in range(16)] for fs in SERVE["filters"]}
+    K = 64
+    slots = [torch.empty(SERVE["side_hi"] * SERVE["side_hi"], dtype=torch.float32).pin_memory() for _ in range(K)]
+    req_flops = [2.0 * side * side * fs * fs for side, fs in shapes]
+
+    t0 = time.time()
+    server = ct.Server(SERVE["budget"], tune=True, max_batch=64, max_launches=3, max_wait_us=200,
+                       filter_min=min(SERVE["filters"]), filter_max=fmax)
+    create_s = time.time() - t0
+
+    def out_view(k, side):
+        pitch = synthetic.round_up(side, 4)
+        return slots[k % K][:side * pitch].view(side, pitch)
+
+    def submit(k):
+        side, fs = shapes[k]
+        return server.submit(out_view(k, side), pool[fs][k % 16], side, side, h_image=h_big,
+                             in_pitch=big.shape[1])
+
+    def run_stream(count, paced):
+        ids = queue.Queue()
+        done = [0]
+        lat = []
+
+        def waiter():
+            for _ in range(count):
+                rid = ids.get()
+                lat.append(server.wait(rid, 120_000_000))
+                done[0] += 1
+        th = threading.Thread(target=waiter)
+        th.start()
+        t_start = time.perf_counter()
+        for k in range(count):
+            if paced:
+                while time.perf_counter() - t_start < arrivals[k]:
+                    pass
+            while k - done[0] >= K:          # output slot k % K still in use
+                time.sleep(0)
+            ids.put(submit(k))
+        th.join()
+        return time.perf_counter() - t_start, lat
+
+    # open loop: the Poisson stream
+    server.reset_stats()
+    wall, lat = run_stream(n, True)
+    st_open = server.stats()
+    # closed loop: saturation
+    n_sat = min(args.sat_requests, n)
+    server.reset_stats()
+    wall_sat, _ = run_stream(n_sat, False)
+    st_sat = server.stats()
+    served_rps = n_sat / wall_sat
+    served_gflops = sum(req_flops[:n_sat]) / wall_sat / 1e9
+
+    # plain per-request path on the same requests
+    cfg = {}
+    ws_img = torch.empty(smax * smax, dtype=torch.float32, device=dev)
+    ws_out = torch.empty(SERVE["side_hi"] * SERVE["side_hi"], dtype=torch.float32, device=dev)
+    for fs in SERVE["filters"]:
+        pr = ct.make_problem(1024, 1024, fs, fs)
+        tab = ct.tune(pr, "full", "anneal", seed=args.seed, max_evals=60, anneal_chains=args.anneal_chains)
+        cfg[fs] = tab.best
+    stream = torch.cuda.Stream(device=dev)
+    n_plain = min(n_sat, 5000)
+    for k in range(20):                      # warm the variants
+        side, fs = shapes[k]
+        pr = ct.make_problem(side, side, fs, fs)
+        ct.conv2d_host_pitched(pr, cfg[fs], h_big.data_ptr(), big.shape[1], pool[fs][0], out_view(k, side).data_ptr(),
+                               synthetic.round_up(side, 4), ws_img.data_ptr(), ws_out.data_ptr(), stream)
+    tp0 = time.perf_counter()
+    for k in range(n_plain):
+        side, fs = shapes[k]
+        pr = ct.make_problem(side, side, fs, fs)
+        ct.conv2d_host_pitched(pr, cfg[fs], h_big.data_ptr(), big.shape[1], pool[fs][k % 16],
+                               out_view(k, side).data_ptr(), synthetic.round_up(side, 4), ws_img.data_ptr(),
+                               ws_out.data_ptr(), stream)
+    wall_plain = time.perf_counter() - tp0
+    plain_rps = n_plain / wall_plain
+    plain_gflops = sum(req_flops[:n_plain]) / wall_plain / 1e9
+    server.close()
+    line = {
+        "metric": METRIC, "value": served_gflops, "unit": "GFLOP/s", "n_gpus": 1, "steps": n_sat, "warmup": 0,
+        "ms_per_step": 1e3 * wall_sat / n_sat, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"served FP32 correlation requests, output sides log-uniform "
+                               f"[{SERVE['side_lo']},{SERVE['side_hi']}], square odd filters "
+                               f"{SERVE['filters'][0]}..{SERVE['filters'][-1]}, seed {SERVE['seed']}, "
+                               f"device budget {SERVE['budget'] >> 30} GiB",
+                   "step": "one request (closed-loop saturation)"},
+        "poisson": {"rate_per_s": SERVE["rate"], "requests": n, "wall_s": wall, "p50_ms": st_open["p50_ms"],
+                    "p99_ms": st_open["p99_ms"], "mean_ms": st_open["mean_ms"], "max_ms": st_open["max_ms"],
+                    "achieved_req_per_s": n / wall, "launches": st_open["launches"],
+                    "mean_batch": st_open["mean_batch"], "peak_mem_bytes": st_open["peak_mem_bytes"]},
+        "saturation": {"requests": n_sat, "served_req_per_s": served_rps, "served_gflops": served_gflops,
+                       "p50_ms": st_sat["p50_ms"], "p99_ms": st_sat["p99_ms"], "mean_batch": st_sat["mean_batch"],
+                       "plain_requests": n_plain, "plain_req_per_s": plain_rps, "plain_gflops": plain_gflops,
+                       "served_vs_plain": served_gflops / plain_gflops},
+        "server_create_s": create_s,
+        "plain_configs": {str(k): v.as_dict() for k, v in cfg.items()},
+        "e2e": {"value": served_gflops, "unit": "GFLOP/s", "note": "host buffers in and out for every request"},
+        "device": info.name.decode(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -167,6 +167,12 @@ CT_API ct_status ct_conv2d(const ct_problem* p, const ct_config* c, const void* 
 CT_API ct_status ct_conv2d_host(const ct_problem* p, const ct_config* c, const void* h_image,
                                 const void* h_filter, float* h_out, void* d_image_ws,
                                 float* d_out_ws, void* stream);
+/* ct_conv2d_host with host rows of their own pitch (elements, >= the row
+ * width; no alignment needed): only the valid columns are copied, with 2D
+ * copies, into the workspaces laid out by p's pitches. */
+CT_API ct_status ct_conv2d_host_pitched(const ct_problem* p, const ct_config* c, const void* h_image,
+                                        int64_t h_in_pitch, const void* h_filter, float* h_out,
+                                        int64_t h_out_pitch, void* d_image_ws, float* d_out_ws, void* stream);
 
 /* ---- search spaces ------------------------------------------------------- */
 
@@ -379,7 +385,8 @@ typedef struct {
     float* h_out;          /* out_h x out_pitch host floats (pinned), written when the request completes */
     const void* h_filter;  /* filter_h x filter_w (float or bf16 bits), copied at submit */
     int32_t out_w, out_h, filter_w, filter_h;
-    int64_t in_pitch, out_pitch;   /* elements; rows of 16-byte multiples */
+    int64_t in_pitch, out_pitch;   /* host row pitches in elements (any value >= the row width); on the
+                                      device the server keeps compact rows and copies with 2D copies */
 } ct_request;
 
 typedef struct {

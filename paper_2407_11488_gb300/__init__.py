@@ -136,6 +136,7 @@ _SIGS = {
     "ct_compile": (i32, [P(Problem), P(Config), P(VariantInfo)]),
     "ct_conv2d": (i32, [P(Problem), P(Config), vp, vp, vp, vp]),
     "ct_conv2d_host": (i32, [P(Problem), P(Config), vp, vp, vp, vp, vp, vp]),
+    "ct_conv2d_host_pitched": (i32, [P(Problem), P(Config), vp, i64, vp, vp, i64, vp, vp, vp]),
     "ct_space_builtin": (i32, [cp, P(vp)]),
     "ct_space_from_json": (i32, [cp, P(vp)]),
     "ct_space_free": (None, [vp]),
@@ -347,6 +348,15 @@ def conv2d_host(problem: Problem, cfg: Config, h_image, h_filter: np.ndarray, h_
                                   h_filter.ctypes.data_as(vp), ctypes.c_void_p(h_out.data_ptr()),
                                   ctypes.c_void_p(d_image_ws.data_ptr()), ctypes.c_void_p(d_out_ws.data_ptr()),
                                   _stream_ptr(stream)))
+
+
+def conv2d_host_pitched(problem: Problem, cfg: Config, h_image, h_in_pitch: int, h_filter: np.ndarray, h_out,
+                        h_out_pitch: int, d_image_ws, d_out_ws, stream=None):
+    """ct_conv2d_host with host rows of their own pitch (2D copies)."""
+    _check(_load().ct_conv2d_host_pitched(ctypes.byref(problem), ctypes.byref(cfg), ctypes.c_void_p(h_image),
+                                          h_in_pitch, h_filter.ctypes.data_as(vp), ctypes.c_void_p(h_out),
+                                          h_out_pitch, ctypes.c_void_p(d_image_ws), ctypes.c_void_p(d_out_ws),
+                                          _stream_ptr(stream)))
 
 
 # ------------------------------------------------------------------ spaces ---

@@ -124,14 +124,16 @@ static HostPipe& host_pipe(int dev)
 
 static constexpr int kMaxBands = 8;
 
-CT_API ct_status ct_conv2d_host(const ct_problem* p, const ct_config* c, const void* h_image, const void* h_filter,
-                                float* h_out, void* d_image_ws, float* d_out_ws, void* stream)
+CT_API ct_status ct_conv2d_host_pitched(const ct_problem* p, const ct_config* c, const void* h_image,
+                                        int64_t h_in_pitch, const void* h_filter, float* h_out, int64_t h_out_pitch,
+                                        void* d_image_ws, float* d_out_ws, void* stream)
 {
     ct_status s = check_problem(p);
     if (s != CT_OK) return s;
     if (!c) return fail(CT_ERR_INVALID_ARG, "config is NULL");
     if (p->out_w == 0 || p->out_h == 0) return CT_OK;
     if (!h_image || !h_out) return fail(CT_ERR_INVALID_ARG, "host image or output is NULL");
+    if (h_in_pitch < in_w(*p) || h_out_pitch < p->out_w) return fail(CT_ERR_INVALID_ARG, "host pitch below the row width");
     if ((s = check_buffers(*p, d_image_ws, h_filter, d_out_ws)) != CT_OK) return s;
     if ((s = require_device()) != CT_OK) return s;
     if ((s = check_config(*p, *c, 0)) != CT_OK) return s;
@@ -169,11 +171,11 @@ CT_API ct_status ct_conv2d_host(const ct_problem* p, const ct_config* c, const v
         const int64_t need = std::min<int64_t>(in_h(*p), y1 + p->filter_h - 1);
         cudaEvent_t e_in = hp.ev[2 + 2 * b], e_comp = hp.ev[3 + 2 * b];
         if (need > copied_rows) {
-            const size_t off = (size_t)(copied_rows * p->in_pitch * es);
-            e = cudaMemcpyAsync((char*)d_image_ws + off, (const char*)h_image + off,
-                                (size_t)((need - copied_rows) * p->in_pitch * es), cudaMemcpyHostToDevice,
-                                hp.copy_in);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(H2D image band)");
+            e = cudaMemcpy2DAsync((char*)d_image_ws + (size_t)(copied_rows * p->in_pitch * es), (size_t)(p->in_pitch * es),
+                                  (const char*)h_image + (size_t)(copied_rows * h_in_pitch * es), (size_t)(h_in_pitch * es),
+                                  (size_t)(in_w(*p) * es), (size_t)(need - copied_rows), cudaMemcpyHostToDevice,
+                                  hp.copy_in);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync(H2D image band)");
             copied_rows = need;
         }
         cudaEventRecord(e_in, hp.copy_in);
@@ -186,14 +188,23 @@ CT_API ct_status ct_conv2d_host(const ct_problem* p, const ct_config* c, const v
             return s;
         cudaEventRecord(e_comp, cs);
         cudaStreamWaitEvent(hp.copy_out, e_comp, 0);
-        e = cudaMemcpyAsync(h_out + y0 * p->out_pitch, d_out_ws + y0 * p->out_pitch,
-                            (size_t)((y1 - y0) * p->out_pitch * 4), cudaMemcpyDeviceToHost, hp.copy_out);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(D2H output band)");
+        e = cudaMemcpy2DAsync(h_out + y0 * h_out_pitch, (size_t)(h_out_pitch * 4), d_out_ws + y0 * p->out_pitch,
+                              (size_t)(p->out_pitch * 4), (size_t)p->out_w * 4, (size_t)(y1 - y0),
+                              cudaMemcpyDeviceToHost, hp.copy_out);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync(D2H output band)");
     }
     cudaEventRecord(done, hp.copy_out);
     cudaStreamWaitEvent(user, done, 0);
     if ((e = cudaStreamSynchronize(user)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return CT_OK;
+}
+
+CT_API ct_status ct_conv2d_host(const ct_problem* p, const ct_config* c, const void* h_image, const void* h_filter,
+                                float* h_out, void* d_image_ws, float* d_out_ws, void* stream)
+{
+    if (!p) return fail(CT_ERR_INVALID_ARG, "problem is NULL");
+    return ct_conv2d_host_pitched(p, c, h_image, p->in_pitch, h_filter, h_out, p->out_pitch, d_image_ws, d_out_ws,
+                                  stream);
 }
 
 // ---------------------------------------------------------------- spaces ---

@@ -94,7 +94,8 @@ struct Request {
     size_t img_off = 0, img_bytes = 0, out_off = 0, out_bytes = 0;
     bool own_image = true;
     const void* d_image = nullptr;
-    int64_t in_pitch = 0;
+    int64_t in_pitch = 0;             // device image pitch (elements)
+    int64_t out_dpitch = 0;           // device output pitch (floats)
     cudaEvent_t ev_in = nullptr;
     double t_submit = 0, t_ready = 0, t_done = 0;
     int status = CT_OK;
@@ -227,7 +228,7 @@ bool ct_server::step_locked()
     while (!pending.empty()) {
         auto& r = pending.front();
         size_t img_off = 0, out_off = 0;
-        const size_t out_bytes = (size_t)r->rq.out_h * (size_t)r->rq.out_pitch * 4;
+        const size_t out_bytes = (size_t)r->rq.out_h * (size_t)r->out_dpitch * 4;
         if (!arena.alloc(std::max<size_t>(out_bytes, 256), out_off)) break;
         if (r->own_image) {
             if (!arena.alloc(std::max<size_t>(r->img_bytes, 256), img_off)) {
@@ -241,9 +242,10 @@ bool ct_server::step_locked()
             r->img_off = img_off;
             r->img_bytes = std::max<size_t>(r->img_bytes, 256);
             r->d_image = base + img_off;
-            cudaMemcpyAsync(base + img_off, r->rq.h_image, (size_t)(r->rq.out_h + r->rq.filter_h - 1) *
-                                                               (size_t)r->in_pitch * (size_t)elem_size(o.dtype),
-                            cudaMemcpyHostToDevice, copy_in);
+            const size_t es = (size_t)elem_size(o.dtype);
+            cudaMemcpy2DAsync(base + img_off, (size_t)r->in_pitch * es, r->rq.h_image, (size_t)r->rq.in_pitch * es,
+                              (size_t)(r->rq.out_w + r->rq.filter_w - 1) * es,
+                              (size_t)(r->rq.out_h + r->rq.filter_h - 1), cudaMemcpyHostToDevice, copy_in);
         }
         cudaEventRecord(r->ev_in, copy_in);
         r->state = RState::Admitted;
@@ -337,7 +339,7 @@ bool ct_server::launch_locked(Launch& L)
         d.in = r.d_image;
         d.out = reinterpret_cast<float*>(base + r.out_off);
         d.in_pitch = r.in_pitch;
-        d.out_pitch = r.rq.out_pitch;
+        d.out_pitch = r.out_dpitch;
         d.out_w = r.rq.out_w;
         d.out_h = r.rq.out_h;
         d.in_w = r.rq.out_w + r.rq.filter_w - 1;
@@ -361,8 +363,9 @@ bool ct_server::launch_locked(Launch& L)
         fatal_msg = last_error();
     }
     for (auto& r : take) {
-        cudaMemcpyAsync((void*)r->rq.h_out, base + r->out_off, (size_t)r->rq.out_h * (size_t)r->rq.out_pitch * 4,
-                        cudaMemcpyDeviceToHost, L.stream);
+        cudaMemcpy2DAsync((void*)r->rq.h_out, (size_t)r->rq.out_pitch * 4, base + r->out_off,
+                          (size_t)r->out_dpitch * 4, (size_t)r->rq.out_w * 4, (size_t)r->rq.out_h,
+                          cudaMemcpyDeviceToHost, L.stream);
         r->state = RState::Running;
     }
     cudaEventRecord(L.done, L.stream);
@@ -535,7 +538,7 @@ CT_API ct_status ct_server_submit(ct_server* s, const ct_request* rq, uint64_t* 
         return fail(CT_ERR_UNSUPPORTED, "filter %dx%d is not served (square sizes %d..%d)", rq->filter_w,
                     rq->filter_h, s->o.filter_min, s->o.filter_max);
     if (rq->out_w <= 0 || rq->out_h <= 0) return fail(CT_ERR_INVALID_ARG, "empty request");
-    if (rq->out_pitch < rq->out_w || (rq->out_pitch * 4) % 16) return fail(CT_ERR_INVALID_ARG, "bad out_pitch");
+    if (rq->out_pitch < rq->out_w) return fail(CT_ERR_INVALID_ARG, "out_pitch < out_w");
     auto r = std::make_shared<Request>();
     r->rq = *rq;
     r->bucket = b;
@@ -553,12 +556,13 @@ CT_API ct_status ct_server_submit(ct_server* s, const ct_request* rq, uint64_t* 
         it->second.users++;
     } else {
         if (!rq->h_image) return fail(CT_ERR_INVALID_ARG, "h_image or image_id is required");
-        if (rq->in_pitch < rq->out_w + rq->filter_w - 1 || (rq->in_pitch * elem_size(s->o.dtype)) % 16)
-            return fail(CT_ERR_INVALID_ARG, "bad in_pitch");
-        r->in_pitch = rq->in_pitch;
-        r->img_bytes = (size_t)(rq->out_h + rq->filter_h - 1) * (size_t)rq->in_pitch * (size_t)elem_size(s->o.dtype);
+        if (rq->in_pitch < rq->out_w + rq->filter_w - 1) return fail(CT_ERR_INVALID_ARG, "in_pitch < input width");
+        const int64_t per16 = 16 / elem_size(s->o.dtype);
+        r->in_pitch = round_up((int64_t)rq->out_w + rq->filter_w - 1, per16);   // compact device rows
+        r->img_bytes = (size_t)(rq->out_h + rq->filter_h - 1) * (size_t)r->in_pitch * (size_t)elem_size(s->o.dtype);
     }
-    const size_t need = r->img_bytes + (size_t)rq->out_h * (size_t)rq->out_pitch * 4 + 1024;
+    r->out_dpitch = round_up(rq->out_w, 4);
+    const size_t need = r->img_bytes + (size_t)rq->out_h * (size_t)r->out_dpitch * 4 + 1024;
     if (need > s->arena.size()) {
         if (!r->own_image) s->images[rq->image_id].users--;
         return fail(CT_ERR_OOM, "request needs %zu bytes, the budget is %zu", need, s->arena.size());

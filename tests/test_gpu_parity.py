@@ -248,3 +248,22 @@ def test_host_entry_point_bands(ctlib, cuda_device):
     for _ in range(2):
         ctlib.conv2d_host(p, c, h_img, np.ascontiguousarray(f), h_out, ws_img, ws_out)
         assert np.array_equal(h_out.numpy()[:, :ow].view(np.uint32), out.view(np.uint32))
+
+
+def test_host_entry_point_pitched(ctlib, cuda_device):
+    """Host rows with a wider pitch than the device rows (2D copies)."""
+    big, f = synthetic.make_problem(13, 1500, 1200, 7, 5)   # host image with a wide pitch
+    ow, oh = 701, 999
+    img = np.ascontiguousarray(big[:oh + 4, :ow + 6])
+    ref, S = oracle.corr2d_f64(img, f, ow, oh)
+    c = ctlib.config(16, 16, 4, 2, 1, 1)
+    p = ctlib.make_problem(ow, oh, 7, 5)
+    h_big = torch.from_numpy(big).pin_memory()
+    h_out = torch.full((oh, 1000), float("nan"), dtype=torch.float32).pin_memory()
+    ws_img = torch.zeros((oh + 4, p.in_pitch), dtype=torch.float32, device=cuda_device)
+    ws_out = torch.zeros((oh, p.out_pitch), dtype=torch.float32, device=cuda_device)
+    ctlib.conv2d_host_pitched(p, c, h_big.data_ptr(), big.shape[1], np.ascontiguousarray(f), h_out.data_ptr(), 1000,
+                              ws_img.data_ptr(), ws_out.data_ptr())
+    got = h_out.numpy()
+    assert_parity(got[:, :ow], ref, S, "pitched host path")
+    assert np.isnan(got[:, ow:]).all()
