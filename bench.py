@@ -292,13 +292,12 @@ def run_ours(args):
                 tab = t
         best = tab.best
         n_valid = tab.info["n_valid_space"]
-        valid = tab.valid()
-        t_sorted = sorted(r["t_med_ms"] for r in valid)
-        perf = sorted(flops / (r["t_med_ms"] * 1e-3) for r in valid)
-        analysis = {"tuned_vs_median": statistics.median(t_sorted) / t_sorted[0],
-                    "frac_within_10pct": sum(1 for t in t_sorted if t <= 1.10 * t_sorted[0]) / len(t_sorted),
-                    "impact": max(perf) / statistics.median(perf),
-                    "analysis_over": f"{len(valid)} configs measured by {args.strategy}"}
+        a = tab.analysis
+        analysis = {"tuned_vs_median": a["tuned_vs_median"], "frac_within_10pct": a["frac_within_10pct"],
+                    "impact": a["impact"],
+                    "proportion_of_centrality": {f"{p:.2f}": v for p, v in a["cp"].items()},
+                    "perf_quantiles_gflops": a["quantiles"],
+                    "analysis_over": f"{a['n_valid']} configs measured by {args.strategy}"}
 
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(int(2 * max(info.l2_bytes, 64 << 20)), dtype=torch.uint8, device=dev)

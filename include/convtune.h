@@ -280,6 +280,27 @@ CT_API ct_status ct_table_info_get(const ct_table* t, ct_table_info* out);
 CT_API ct_status ct_table_write(const ct_table* t, const char* path);
 CT_API void ct_table_free(ct_table* t);
 
+/* Analysis of a timing table (the configurations it measured):
+ *   tuning impact = optimum performance / median performance (Sec. 4,
+ *   Table 4; median of an even count = mean of the two middle values),
+ *   tuned/median time, the fraction within 10 % of the optimum, performance
+ *   quantiles p0/p10/p25/p50/p75/p90/p100 (linear interpolation), and the
+ *   proportion of centrality C_p of Eq. 1 for each p: PageRank (damping 0.85,
+ *   sinks spread uniformly) on the fitness flow graph whose edges join
+ *   neighbouring configurations (one parameter one step apart in the space's
+ *   value lists) towards the faster one; C_p = centrality of the local minima
+ *   with time <= (1+p) * optimum over that of all local minima.  flops > 0
+ *   expresses performance in GFLOP/s (else 1/time). */
+typedef struct {
+    int64_t n_valid, n_minima, best_index;
+    double p_max, p_median, impact, tuned_vs_median, frac_within_10pct;
+    double quantiles[7];
+    int32_t n_p, reserved;
+    double p[16], cp[16];
+} ct_analysis;
+CT_API ct_status ct_table_analyze(const ct_table* t, const ct_space* s, double flops, const double* p_values,
+                                  int32_t n_p, ct_analysis* out);
+
 
 /* ---- batched uneven problems (one persistent launch) ---------------------
  *

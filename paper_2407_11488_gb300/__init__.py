@@ -124,6 +124,12 @@ class ServerStats(ctypes.Structure):
                 ("req_per_s", dbl), ("gflops", dbl), ("peak_mem_bytes", i64)]
 
 
+class Analysis(ctypes.Structure):
+    _fields_ = [("n_valid", i64), ("n_minima", i64), ("best_index", i64), ("p_max", dbl), ("p_median", dbl),
+                ("impact", dbl), ("tuned_vs_median", dbl), ("frac_within_10pct", dbl), ("quantiles", dbl * 7),
+                ("n_p", i32), ("reserved", i32), ("p", dbl * 16), ("cp", dbl * 16)]
+
+
 P = ctypes.POINTER
 _SIGS = {
     "ct_version": (cp, []),
@@ -149,6 +155,7 @@ _SIGS = {
     "ct_table_info_get": (i32, [vp, P(TableInfo)]),
     "ct_table_write": (i32, [vp, cp]),
     "ct_table_free": (None, [vp]),
+    "ct_table_analyze": (i32, [vp, vp, dbl, P(dbl), i32, P(Analysis)]),
     "ct_batch_create": (i32, [P(BatchItem), i32, P(BatchOpts), P(vp)]),
     "ct_batch_run": (i32, [vp, vp]),
     "ct_batch_info_get": (i32, [vp, P(BatchInfo)]),
@@ -404,6 +411,7 @@ class Table:
     rows: list
     info: dict
     best: Config | None
+    analysis: dict | None = None
 
     def valid(self):
         return [r for r in self.rows if r["status"] == 0 and math.isfinite(r["t_med_ms"])]
@@ -416,7 +424,22 @@ def _row_dict(r: Row) -> dict:
     return d
 
 
-def _collect(t, best, write_path=None) -> Table:
+P_VALUES = (0.0, 0.01, 0.02, 0.05, 0.10, 0.15)
+
+
+def _analysis(t, space, flops):
+    a = Analysis()
+    pv = (dbl * len(P_VALUES))(*P_VALUES)
+    if _load().ct_table_analyze(t, space.handle, flops, pv, len(P_VALUES), ctypes.byref(a)) != CT_OK:
+        return None
+    d = {k: getattr(a, k) for k in ("n_valid", "n_minima", "best_index", "p_max", "p_median", "impact",
+                                     "tuned_vs_median", "frac_within_10pct")}
+    d["quantiles"] = dict(zip((0, 10, 25, 50, 75, 90, 100), list(a.quantiles)))
+    d["cp"] = {P_VALUES[k]: a.cp[k] for k in range(a.n_p)}
+    return d
+
+
+def _collect(t, best, write_path=None, space=None, flops=0.0) -> Table:
     L = _load()
     try:
         if write_path:
@@ -429,7 +452,7 @@ def _collect(t, best, write_path=None) -> Table:
             _check(L.ct_table_row(t, i, ctypes.byref(r)))
             rows.append(_row_dict(r))
         infod = {k: getattr(info, k) for k, _ in TableInfo._fields_}
-        return Table(rows, infod, best)
+        return Table(rows, infod, best, _analysis(t, space, flops) if space is not None else None)
     finally:
         L.ct_table_free(t)
 
@@ -456,7 +479,8 @@ def tune(problem: Problem, space="small", strategy="brute", *, image=None, filt=
                          ctypes.c_void_p(out.data_ptr()) if out is not None else None,
                          ctypes.byref(best), ctypes.byref(t))
     if t.value:
-        table = _collect(t, best if st == CT_OK else None, write_path)
+        flops = 2.0 * problem.out_w * problem.out_h * problem.filter_w * problem.filter_h
+        table = _collect(t, best if st == CT_OK else None, write_path, sp, flops)
         if st != CT_OK:
             raise CTError(st, _load().ct_last_error().decode(errors="replace"))
         return table
@@ -475,7 +499,8 @@ def tune_replay(problem: Problem, space, strategy, times_ms, **opts) -> Table:
     st = _load().ct_tune_replay(ctypes.byref(problem), sp.handle, STRATEGIES[strategy], ctypes.byref(o),
                                 arr.ctypes.data_as(P(dbl)), len(arr), ctypes.byref(best), ctypes.byref(t))
     if t.value:
-        return _collect(t, best if st == CT_OK else None)
+        flops = 2.0 * problem.out_w * problem.out_h * problem.filter_w * problem.filter_h
+        return _collect(t, best if st == CT_OK else None, None, sp, flops)
     _check(st)
     raise CTError(-5, "ct_tune_replay returned no table")
 

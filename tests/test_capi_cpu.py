@@ -276,3 +276,38 @@ def test_server_without_gpu(ctlib):
     import ctypes
     h = ctlib.vp()
     assert ctlib.lib().ct_server_create(None, ctypes.byref(h)) == -1
+
+
+def _oracle_analysis(table, space_name, flops, p_values):
+    rows = oracle_rows(table)
+    st = analysis.stats(rows, flops)
+    ok = {r["index"]: r["t"] for r in analysis.valid_rows(rows)}
+    cfg_of = {r["index"]: {"block_x": r["block_x"], "block_y": r["block_y"], "tile_x": r["tile_x"],
+                           "tile_y": r["tile_y"], "smem": r["use_smem"], "unroll": r["unroll"]} for r in table.rows}
+    nb = lambda i: [ospace.canonical_index(space_name, c) for c in ospace.neighbours(space_name, cfg_of[i])]
+    edges = analysis.fitness_flow_graph(list(ok), ok, nb)
+    c = analysis.pagerank(edges)
+    cps = {p: analysis.proportion_of_centrality(edges, ok, p, c) for p in p_values}
+    return st, edges, cps
+
+
+@pytest.mark.parametrize("strategy", ["brute", "random"])
+def test_table_analysis_matches_oracle(ctlib, strategy):
+    p = ctlib.make_problem(4096, 4096, 17, 17)
+    times = landscape("full", 17, 17, 21, fail_every=53)
+    tab = ctlib.tune_replay(p, "full", strategy, times, seed=4)
+    a = tab.analysis
+    flops = 2.0 * 4096 * 4096 * 289
+    # oracle performance = flops / t_ms; / 1e6 turns flops per ms into GFLOP/s
+    st, edges, cps = _oracle_analysis(tab, "full", flops / 1e6, ctlib.P_VALUES)
+    assert a["n_valid"] == st["n_valid"]
+    assert a["best_index"] == st["best_index"]
+    for k, ko in (("p_max", "p_max"), ("p_median", "p_median"), ("impact", "impact"),
+                  ("tuned_vs_median", "tuned_vs_median_time"), ("frac_within_10pct", "frac_within_10pct")):
+        assert a[k] == pytest.approx(st[ko], rel=1e-12), k
+    for q, v in st["quantiles"].items():
+        assert a["quantiles"][q] == pytest.approx(v, rel=1e-12)
+    assert a["n_minima"] == sum(1 for out in edges.values() if not out)
+    for pv in ctlib.P_VALUES:
+        assert a["cp"][pv] == pytest.approx(cps[pv], abs=1e-9), pv
+    assert a["cp"][0.0] <= a["cp"][0.05] <= a["cp"][0.15] <= 1.0
