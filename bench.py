@@ -36,9 +36,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "tuned conv2d GFLOP/s (%FP32 peak), tuned/default speedup, batched p99 latency"
 WORKLOADS = {
-    # name: (out_w, out_h, filter, seed, space)
-    "full": (4096, 4096, 17, 1, "full"),
-    "small": (256, 256, 5, 0, "small"),
+    # name: (out_w, out_h, filter, seed, space, storage)
+    "full": (4096, 4096, 17, 1, "full", "f32"),
+    "small": (256, 256, 5, 0, "small", "f32"),
+    "bf16": (4096, 4096, 17, 4, "full", "bf16"),
+    "bf16_small": (1024, 1024, 9, 4, "full", "bf16"),
 }
 BATCH = {"count": 64, "side_lo": 128, "side_hi": 4096, "filters": (3, 5, 7, 11, 17), "seed": 2}
 SERVE = {"rate": 2000.0, "side_lo": 64, "side_hi": 2048, "filters": (3, 5, 7, 9, 11, 13, 15, 17), "seed": 3,
@@ -178,7 +180,7 @@ def run_reference(args):
     import oracle
     import synthetic
     oracle.build()
-    ow, oh, fs, seed, _ = WORKLOADS.get(args.workload, WORKLOADS["full"])
+    ow, oh, fs, seed = WORKLOADS.get(args.workload, WORKLOADS["full"])[:4]
     img, f = synthetic.make_problem(seed, ow, oh, fs, fs)
     steps = args.steps + args.warmup
     dt = cpu_rate_sample(img, f, ow, 8) / 8.0            # seconds per output row
@@ -214,7 +216,7 @@ def kernel_sha():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(cfg_tuple):
+def measured_traffic(cfg_tuple, workload):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the same kernel source and configuration; else None."""
     path = os.path.join(ROOT, "profiles", "traffic_corr2d.json")
@@ -224,7 +226,8 @@ def measured_traffic(cfg_tuple):
     except (OSError, ValueError):
         return None
     for r in rec.get("captures", []):
-        if r.get("kernel_sha") == kernel_sha() and tuple(r.get("config", ())) == tuple(cfg_tuple):
+        if (r.get("kernel_sha") == kernel_sha() and tuple(r.get("config", ())) == tuple(cfg_tuple)
+                and r.get("workload", "full") == workload):
             return float(r["dram_bytes_per_launch"])
     return None
 
@@ -263,10 +266,18 @@ def run_ours(args):
     sm_max_mhz = float(pk.get("sm_max_mhz") or (info.clock_max_khz / 1e3) or 2070.0)
     fp32_peak = info.sm_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12   # TFLOP/s
 
-    ow, oh, fs, seed, space = WORKLOADS[args.workload]
-    img, f = synthetic.make_problem(seed, ow, oh, fs, fs)
+    ow, oh, fs, seed, space, storage = WORKLOADS[args.workload]
+    bf16 = storage == "bf16"
+    img, f = synthetic.make_problem(seed, ow, oh, fs, fs, pitch_align=8 if bf16 else 4)
     flops = 2.0 * ow * oh * fs * fs
-    d_img = torch.from_numpy(img).to(dev)
+    if bf16:
+        # BF16 storage: the inputs rounded to nearest-even bf16, FP32 accumulation
+        img_t = torch.from_numpy(img).to(torch.bfloat16)
+        f = torch.from_numpy(f).to(torch.bfloat16)
+        img = img_t.float().numpy()            # the values the GPU sees, widened exactly
+        d_img = img_t.to(dev)
+    else:
+        d_img = torch.from_numpy(img).to(dev)
     p = ct.problem_for(d_img, f, in_w=ow + fs - 1)
     d_out = torch.empty((oh, p.out_pitch), dtype=torch.float32, device=dev)
 
@@ -301,7 +312,7 @@ def run_ours(args):
 
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(int(2 * max(info.l2_bytes, 64 << 20)), dtype=torch.uint8, device=dev)
-    hf = np.ascontiguousarray(f)
+    hf = ct._filter_bytes(f, p.dtype)
 
     def timed_loop(cfg, k, w):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
@@ -341,7 +352,7 @@ def run_ours(args):
     value = world * flops / (t_step * 1e-3) / 1e9
 
     # ---- end to end through the host-buffer entry point
-    h_img = torch.from_numpy(img).pin_memory()
+    h_img = (img_t if bf16 else torch.from_numpy(img)).pin_memory()
     h_out = torch.empty((oh, p.out_pitch), dtype=torch.float32).pin_memory()
     e_steps = max(10, min(args.steps, 500))
     with torch.cuda.stream(stream):
@@ -359,7 +370,7 @@ def run_ours(args):
         clk["note"] = "no sample inside the timed loop; samples from tuning, timed and e2e phases"
 
     achieved = flops / (t_step * 1e-3) / 1e12
-    traffic = measured_traffic(best.as_tuple())
+    traffic = measured_traffic(best.as_tuple(), args.workload)
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": traffic,
             "peak_basis": f"{info.sm_count} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 x {sm_max_mhz:.0f} MHz "
@@ -372,6 +383,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"corr2d out {ow}x{oh}, filter {fs}x{fs}, uniform[-1,1) seed {seed}",
+                   "storage": storage,
                    "space": f"{space} ({n_valid} valid configs)",
                    "strategy": "fixed --config" if args.config else args.strategy,
                    "tuned_config": best.as_dict(),
@@ -386,7 +398,7 @@ def run_ours(args):
                        "best_ms": v["best_ms"], "cold_cache": bool(args.cold_cache)}
                    for k, v in tuning.items()},
         "roofline": roof,
-        "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": int(img.nbytes),
+        "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h_img.numel() * h_img.element_size()),
                 "d2h_bytes_per_step": int(h_out.numel() * 4), "ms_per_step": te * 1e3},
         "gpu_launches": args.steps,
         "clocks": clk,
@@ -395,7 +407,8 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        line["cpu_baseline"] = cpu_baseline(img, f, ow, oh, args.cpu_seconds)
+        f_np = f.float().numpy() if hasattr(f, "float") else f
+        line["cpu_baseline"] = cpu_baseline(img, f_np, ow, oh, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
