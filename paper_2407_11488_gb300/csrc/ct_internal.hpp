@@ -153,6 +153,8 @@ public:
     void forget(const VariantKey& k);
     void forget(uint64_t key);
     const std::string& cache_dir() const { return cache_dir_; }
+    size_t queued();
+    size_t threads() const { return threads_.size(); }
 private:
     struct Item {
         uint64_t key;

@@ -66,6 +66,12 @@ std::shared_future<VariantPtr> CompilePool::request(uint64_t key, Job job, bool 
 
 void CompilePool::forget(const VariantKey& k) { forget(k.packed()); }
 
+size_t CompilePool::queued()
+{
+    std::lock_guard<std::mutex> g(mu_);
+    return queue_.size();
+}
+
 void CompilePool::forget(uint64_t key)
 {
     std::lock_guard<std::mutex> g(mu_);
@@ -117,6 +123,7 @@ class Evaluator {
 public:
     virtual ~Evaluator() = default;
     virtual void prefetch(const Entry&, bool urgent = false) { (void)urgent; }
+    virtual bool queue_short() const { return true; }
     virtual Measure eval(const Entry& e) = 0;
     double compile_wait_ms = 0, compile_cpu_ms = 0, bench_ms = 0;
     bool abort = false;   // set after an unrecoverable device error
@@ -163,6 +170,7 @@ public:
     }
     VariantKey key(const Entry& e) const { return VariantKey{e.cfg, p_.filter_w, p_.filter_h, p_.dtype}; }
     void prefetch(const Entry& e, bool urgent) override { pool_.request(key(e), urgent); }
+    bool queue_short() const override { return pool_.queued() < 2 * pool_.threads(); }
 
     Measure eval(const Entry& e) override
     {
@@ -420,6 +428,7 @@ public:
     }
 
     bool is_valid(int64_t idx) const { return pos_.count(idx) != 0; }
+    bool queue_short() const { return ev_.queue_short(); }
     const Entry& entry(int64_t idx) const { return valid_[pos_.at(idx)]; }
     bool visited(int64_t idx) const { return row_of_.count(idx) != 0; }
     size_t n_rows() const { return rows.size(); }
@@ -581,6 +590,13 @@ static void run_anneal(Driver& d, const Space& s, const std::vector<Entry>& vali
             }
         }
         for (const Entry* c : cand) d.prefetch(*c, true);
+        // speculative, behind the urgent candidates: the unmeasured neighbours
+        // of every walker's point and candidate (the next proposals come from
+        // them), while the compile queue is short
+        for (size_t m = 0; m < w.size() && d.queue_short(); ++m) {
+            for (int64_t i : neighbours(s, d, w[m].cur->cfg)) d.prefetch(d.entry(i), false);
+            for (int64_t i : neighbours(s, d, cand[m]->cfg)) d.prefetch(d.entry(i), false);
+        }
         for (size_t m = 0; m < w.size() && (int64_t)d.n_rows() < budget; ++m) {
             Walker& x = w[m];
             bool fresh_eval = false;
