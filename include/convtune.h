@@ -173,6 +173,17 @@ CT_API ct_status ct_conv2d_host(const ct_problem* p, const ct_config* c, const v
 CT_API ct_status ct_conv2d_host_pitched(const ct_problem* p, const ct_config* c, const void* h_image,
                                         int64_t h_in_pitch, const void* h_filter, float* h_out,
                                         int64_t h_out_pitch, void* d_image_ws, float* d_out_ws, void* stream);
+/* Asynchronous form of ct_conv2d_host_pitched: the work starts after what is
+ * queued on `stream`, the call returns once it is enqueued, and completion
+ * (output in h_out) is recorded on the caller's CUDA event done_event
+ * (cudaEvent_t); `stream` is not made to wait.  Consecutive calls therefore
+ * overlap (the copy-in of one under the copy-out of the previous): the
+ * caller must give overlapping calls different workspaces and host buffers
+ * and must not touch them before done_event completes. */
+CT_API ct_status ct_conv2d_host_async(const ct_problem* p, const ct_config* c, const void* h_image,
+                                      int64_t h_in_pitch, const void* h_filter, float* h_out,
+                                      int64_t h_out_pitch, void* d_image_ws, float* d_out_ws, void* stream,
+                                      void* done_event);
 
 /* ---- search spaces ------------------------------------------------------- */
 

@@ -143,6 +143,7 @@ _SIGS = {
     "ct_conv2d": (i32, [P(Problem), P(Config), vp, vp, vp, vp]),
     "ct_conv2d_host": (i32, [P(Problem), P(Config), vp, vp, vp, vp, vp, vp]),
     "ct_conv2d_host_pitched": (i32, [P(Problem), P(Config), vp, i64, vp, vp, i64, vp, vp, vp]),
+    "ct_conv2d_host_async": (i32, [P(Problem), P(Config), vp, i64, vp, vp, i64, vp, vp, vp, vp]),
     "ct_space_builtin": (i32, [cp, P(vp)]),
     "ct_space_from_json": (i32, [cp, P(vp)]),
     "ct_space_free": (None, [vp]),
@@ -364,6 +365,16 @@ def conv2d_host_pitched(problem: Problem, cfg: Config, h_image, h_in_pitch: int,
                                           h_in_pitch, h_filter.ctypes.data_as(vp), ctypes.c_void_p(h_out),
                                           h_out_pitch, ctypes.c_void_p(d_image_ws), ctypes.c_void_p(d_out_ws),
                                           _stream_ptr(stream)))
+
+
+def conv2d_host_async(problem: Problem, cfg: Config, h_image, h_in_pitch: int, h_filter: np.ndarray, h_out,
+                      h_out_pitch: int, d_image_ws, d_out_ws, done_event, stream=None):
+    """ct_conv2d_host_async: enqueue, signal completion on done_event (a
+    torch.cuda.Event); the caller keeps the buffers untouched until then."""
+    _check(_load().ct_conv2d_host_async(ctypes.byref(problem), ctypes.byref(cfg), ctypes.c_void_p(h_image),
+                                        h_in_pitch, h_filter.ctypes.data_as(vp), ctypes.c_void_p(h_out), h_out_pitch,
+                                        ctypes.c_void_p(d_image_ws), ctypes.c_void_p(d_out_ws), _stream_ptr(stream),
+                                        ctypes.c_void_p(done_event.cuda_event)))
 
 
 # ------------------------------------------------------------------ spaces ---

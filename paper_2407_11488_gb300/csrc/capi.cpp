@@ -124,9 +124,9 @@ static HostPipe& host_pipe(int dev)
 
 static constexpr int kMaxBands = 8;
 
-CT_API ct_status ct_conv2d_host_pitched(const ct_problem* p, const ct_config* c, const void* h_image,
-                                        int64_t h_in_pitch, const void* h_filter, float* h_out, int64_t h_out_pitch,
-                                        void* d_image_ws, float* d_out_ws, void* stream)
+static ct_status host_pipeline(const ct_problem* p, const ct_config* c, const void* h_image, int64_t h_in_pitch,
+                               const void* h_filter, float* h_out, int64_t h_out_pitch, void* d_image_ws,
+                               float* d_out_ws, void* stream, cudaEvent_t done_event)
 {
     ct_status s = check_problem(p);
     if (s != CT_OK) return s;
@@ -193,10 +193,31 @@ CT_API ct_status ct_conv2d_host_pitched(const ct_problem* p, const ct_config* c,
                               cudaMemcpyDeviceToHost, hp.copy_out);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync(D2H output band)");
     }
+    if (done_event) {   // asynchronous form: completion is signalled on the caller's event only
+        if ((e = cudaEventRecord(done_event, hp.copy_out)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        return CT_OK;
+    }
     cudaEventRecord(done, hp.copy_out);
     cudaStreamWaitEvent(user, done, 0);
     if ((e = cudaStreamSynchronize(user)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return CT_OK;
+}
+
+CT_API ct_status ct_conv2d_host_pitched(const ct_problem* p, const ct_config* c, const void* h_image,
+                                        int64_t h_in_pitch, const void* h_filter, float* h_out, int64_t h_out_pitch,
+                                        void* d_image_ws, float* d_out_ws, void* stream)
+{
+    return host_pipeline(p, c, h_image, h_in_pitch, h_filter, h_out, h_out_pitch, d_image_ws, d_out_ws, stream,
+                         nullptr);
+}
+
+CT_API ct_status ct_conv2d_host_async(const ct_problem* p, const ct_config* c, const void* h_image,
+                                      int64_t h_in_pitch, const void* h_filter, float* h_out, int64_t h_out_pitch,
+                                      void* d_image_ws, float* d_out_ws, void* stream, void* done_event)
+{
+    if (!done_event) return fail(CT_ERR_INVALID_ARG, "done_event is NULL");
+    return host_pipeline(p, c, h_image, h_in_pitch, h_filter, h_out, h_out_pitch, d_image_ws, d_out_ws, stream,
+                         (cudaEvent_t)done_event);
 }
 
 CT_API ct_status ct_conv2d_host(const ct_problem* p, const ct_config* c, const void* h_image, const void* h_filter,

@@ -300,3 +300,25 @@ def test_bf16_error_against_fp32_inputs(ctlib, cuda_device, shape):
             first = got
         else:
             assert np.array_equal(got, first)
+
+
+def test_host_entry_point_async_overlapping_calls(ctlib, cuda_device):
+    """Two asynchronous host-buffer calls in flight at once (distinct buffers)
+    give the same bits as the synchronous path."""
+    ow, oh, fw, fh = 1500, 1300, 9, 9
+    probs = [synthetic.make_problem(21 + k, ow, oh, fw, fh) for k in range(2)]
+    p = ctlib.make_problem(ow, oh, fw, fh)
+    c = ctlib.config(16, 16, 4, 2, 1, 1)
+    h_imgs = [torch.from_numpy(img).pin_memory() for img, _ in probs]
+    h_outs = [torch.full((oh, p.out_pitch), float("nan")).pin_memory() for _ in range(2)]
+    ws_i = [torch.empty((oh + fh - 1, p.in_pitch), device=cuda_device) for _ in range(2)]
+    ws_o = [torch.empty((oh, p.out_pitch), device=cuda_device) for _ in range(2)]
+    ev = [torch.cuda.Event(), torch.cuda.Event()]
+    for k in range(2):
+        ctlib.conv2d_host_async(p, c, h_imgs[k].data_ptr(), p.in_pitch, np.ascontiguousarray(probs[k][1]),
+                                h_outs[k].data_ptr(), p.out_pitch, ws_i[k].data_ptr(), ws_o[k].data_ptr(), ev[k])
+    for k in range(2):
+        ev[k].synchronize()
+        d = upload_image(probs[k][0], cuda_device)
+        ref, ok = run_config(ctlib, d, probs[k][1], c, ow, oh, in_w=ow + fw - 1)
+        assert np.array_equal(h_outs[k].numpy()[:, :ow].view(np.uint32), ref.view(np.uint32))
