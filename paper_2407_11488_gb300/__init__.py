@@ -371,6 +371,9 @@ def conv2d_host_async(problem: Problem, cfg: Config, h_image, h_in_pitch: int, h
                       h_out_pitch: int, d_image_ws, d_out_ws, done_event, stream=None):
     """ct_conv2d_host_async: enqueue, signal completion on done_event (a
     torch.cuda.Event); the caller keeps the buffers untouched until then."""
+    import torch
+    if done_event.cuda_event == 0:          # torch creates the event on its first record
+        done_event.record(torch.cuda.current_stream())
     _check(_load().ct_conv2d_host_async(ctypes.byref(problem), ctypes.byref(cfg), ctypes.c_void_p(h_image),
                                         h_in_pitch, h_filter.ctypes.data_as(vp), ctypes.c_void_p(h_out), h_out_pitch,
                                         ctypes.c_void_p(d_image_ws), ctypes.c_void_p(d_out_ws), _stream_ptr(stream),
