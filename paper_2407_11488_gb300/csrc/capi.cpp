@@ -171,11 +171,16 @@ static ct_status host_pipeline(const ct_problem* p, const ct_config* c, const vo
         const int64_t need = std::min<int64_t>(in_h(*p), y1 + p->filter_h - 1);
         cudaEvent_t e_in = hp.ev[2 + 2 * b], e_comp = hp.ev[3 + 2 * b];
         if (need > copied_rows) {
-            e = cudaMemcpy2DAsync((char*)d_image_ws + (size_t)(copied_rows * p->in_pitch * es), (size_t)(p->in_pitch * es),
-                                  (const char*)h_image + (size_t)(copied_rows * h_in_pitch * es), (size_t)(h_in_pitch * es),
-                                  (size_t)(in_w(*p) * es), (size_t)(need - copied_rows), cudaMemcpyHostToDevice,
-                                  hp.copy_in);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync(H2D image band)");
+            char* dst = (char*)d_image_ws + (size_t)(copied_rows * p->in_pitch * es);
+            const char* src = (const char*)h_image + (size_t)(copied_rows * h_in_pitch * es);
+            if (h_in_pitch == p->in_pitch)   // same row layout: one contiguous copy
+                e = cudaMemcpyAsync(dst, src, (size_t)((need - copied_rows) * p->in_pitch * es),
+                                    cudaMemcpyHostToDevice, hp.copy_in);
+            else
+                e = cudaMemcpy2DAsync(dst, (size_t)(p->in_pitch * es), src, (size_t)(h_in_pitch * es),
+                                      (size_t)(in_w(*p) * es), (size_t)(need - copied_rows), cudaMemcpyHostToDevice,
+                                      hp.copy_in);
+            if (e != cudaSuccess) return cuda_fail(e, "copy of an image band to the device");
             copied_rows = need;
         }
         cudaEventRecord(e_in, hp.copy_in);
@@ -188,10 +193,14 @@ static ct_status host_pipeline(const ct_problem* p, const ct_config* c, const vo
             return s;
         cudaEventRecord(e_comp, cs);
         cudaStreamWaitEvent(hp.copy_out, e_comp, 0);
-        e = cudaMemcpy2DAsync(h_out + y0 * h_out_pitch, (size_t)(h_out_pitch * 4), d_out_ws + y0 * p->out_pitch,
-                              (size_t)(p->out_pitch * 4), (size_t)p->out_w * 4, (size_t)(y1 - y0),
-                              cudaMemcpyDeviceToHost, hp.copy_out);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync(D2H output band)");
+        if (h_out_pitch == p->out_pitch)
+            e = cudaMemcpyAsync(h_out + y0 * h_out_pitch, d_out_ws + y0 * p->out_pitch,
+                                (size_t)((y1 - y0) * p->out_pitch * 4), cudaMemcpyDeviceToHost, hp.copy_out);
+        else
+            e = cudaMemcpy2DAsync(h_out + y0 * h_out_pitch, (size_t)(h_out_pitch * 4), d_out_ws + y0 * p->out_pitch,
+                                  (size_t)(p->out_pitch * 4), (size_t)p->out_w * 4, (size_t)(y1 - y0),
+                                  cudaMemcpyDeviceToHost, hp.copy_out);
+        if (e != cudaSuccess) return cuda_fail(e, "copy of an output band to the host");
     }
     if (done_event) {   // asynchronous form: completion is signalled on the caller's event only
         if ((e = cudaEventRecord(done_event, hp.copy_out)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
