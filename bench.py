@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=100000, help="serve: requests of the Poisson stream")
     ap.add_argument("--sat-requests", type=int, default=20000, help="serve: requests of the saturation runs")
     ap.add_argument("--anneal-chains", type=int, default=4)
+    ap.add_argument("--batch-filter", type=int, default=0,
+                    help="batch: keep only the problems with this filter size (diagnostics)")
     ap.add_argument("--batch-plain", choices=["tune", "skip"], default="tune",
                     help="skip: time only the batched path (profiling)")
     ap.add_argument("--batch-plain-evals", type=int, default=120,
@@ -74,6 +76,21 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
+
+
+def aggregate_over_ranks(t_step_ms, flops_per_rank, device=None):
+    """Whole-job throughput of N replicas: the slowest rank's step time (max
+    over ranks) and value = all ranks' work / that time, in GFLOP/s.  Single
+    process: no collective."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return t_step_ms, flops_per_rank / (t_step_ms * 1e-3) / 1e9
+    world = dist.get_world_size()
+    t = torch.tensor([float(t_step_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    return t_max, world * flops_per_rank / (t_max * 1e-3) / 1e9
 
 
 def dist_env():
@@ -344,12 +361,7 @@ def run_ours(args):
     clocks.mark("timed_end")
     default = ct.default_config()
     ms_def, _, _ = timed_loop(default, max(50, args.steps // 10), 5)
-    t_step = sum(ms) / len(ms)
-    if world > 1:
-        t = torch.tensor([t_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(t.item())
-    value = world * flops / (t_step * 1e-3) / 1e9
+    t_step, value = aggregate_over_ranks(sum(ms) / len(ms), flops, dev)
 
     # ---- end to end through the host-buffer entry point: every step copies
     # the image in and the result out; consecutive steps overlap (two sets of
@@ -463,13 +475,19 @@ def run_batch(args):
     fp32_peak = info.sm_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     shapes = synthetic.uneven_batch(BATCH["seed"], BATCH["count"], BATCH["side_lo"], BATCH["side_hi"],
                                     BATCH["filters"])
+    keep = [k for k, (_, fs) in enumerate(shapes) if not args.batch_filter or fs == args.batch_filter]
     probs = []
-    for k, (side, fs) in enumerate(shapes):
+    for k in keep:
+        side, fs = shapes[k]
         img, f = synthetic.make_problem(BATCH["seed"] * 100000 + k, side, side, fs, fs)
         d_img = torch.from_numpy(img).to(dev)
         out = torch.empty((side, synthetic.round_up(side, 4)), dtype=torch.float32, device=dev)
         probs.append((img, np.ascontiguousarray(f), d_img, out, side, fs))
+    shapes = [shapes[k] for k in keep]
     flops = sum(2.0 * side * side * fs * fs for side, fs in shapes)
+    peak_s = sum(max(2.0 * s * s * f * f / (fp32_peak * 1e12),
+                     (4.0 * (s + f - 1) ** 2 + 4.0 * s * s) / (float(pk.get("hbm_gbs") or 6680.0) * 1e9))
+                 for s, f in shapes)
 
     # plain path: tune once per filter size on that size's largest problem
     t0 = time.time()
@@ -571,10 +589,12 @@ def run_batch(args):
                                f"[{BATCH['side_lo']},{BATCH['side_hi']}], filters {list(BATCH['filters'])}, "
                                f"seed {BATCH['seed']}",
                    "total_gflop": flops / 1e9, "l2": "flushed between timed iterations",
+                   "filter_subset": args.batch_filter or None,
                    "parallelism": f"replicas x{world}"},
         "batched_p50_ms": statistics.median(ms_batch), "batched_p99_ms": p99,
         "plain_gflops": world * flops / (t_p * 1e-3) / 1e9, "plain_ms_per_step": t_p,
         "batched_vs_plain": t_p / t_b, "bit_identical_to_plain": identical,
+        "composite_bound_ms": peak_s * 1e3, "batched_frac_of_bound": peak_s * 1e3 / t_b,
         "batch": {"buckets": batch.buckets(), **binfo, "plan_s": batch_plan_s},
         "plain_tuning": {"wall_s": plain_tune_s, **tuning},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",

@@ -1,0 +1,54 @@
+"""The N > 1 host logic of bench.py on CPU: two gloo ranks report different
+step times; both see the slowest one, and the value counts both ranks' work."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, world, port, q):
+    import sys
+    import torch.distributed as dist
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    assert bench.dist_env() == (rank, world, rank)
+    t_ms = 2.0 if rank == 0 else 3.0          # rank 1 is the slow one
+    dist.barrier()
+    t_max, value = bench.aggregate_over_ranks(t_ms, 6e9)
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, t_max, value))
+
+
+def test_two_gloo_ranks_take_the_slowest_step():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=5) for _ in range(2))
+    for rank, t_max, value in res:
+        assert t_max == 3.0
+        assert value == pytest.approx(2 * 6e9 / 3e-3 / 1e9)
+
+
+def test_single_process_needs_no_collective():
+    import bench
+    t, v = bench.aggregate_over_ranks(2.0, 4e9)
+    assert t == 2.0 and v == pytest.approx(4e9 / 2e-3 / 1e9)
