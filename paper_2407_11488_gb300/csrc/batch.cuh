@@ -70,9 +70,9 @@ __device__ __forceinline__ void ct_cp_wait()
 
 // Shared-memory buffer of one work item: filter taps (FH rows of FWP floats,
 // zero padded), then the input tile plus halo (HH rows of SW floats).
-// stage() and compute() are inlined into the kernel's switch; the
-// __launch_bounds__ minimum of CT_MINB blocks per SM caps the registers of
-// the combined body (without the cap, ten inlined buckets took 120).
+// stage() and compute() are real calls, not inlined: each bucket's routine
+// then gets its own register allocation and the kernel needs only the
+// largest of them, instead of the union a single inlined body would hold.
 template <int BX, int TX, int TY, int FW, int FH, int UN>
 struct CtTile {
     static constexpr int BY = CT_NT / BX;
@@ -85,7 +85,7 @@ struct CtTile {
     static constexpr int WWV = ct_rup(WW, VW);
 
     // Starts the copies of one item into buf (asynchronous for FP32 images).
-    static __device__ __forceinline__ void stage(const CtBatchProblem& pr, const float* __restrict__ filters,
+    static __device__ __noinline__ void stage(const CtBatchProblem& pr, const float* __restrict__ filters,
                                                  int tile, float* buf)
     {
         const int tid = threadIdx.x;
@@ -152,7 +152,7 @@ struct CtTile {
     }
 
     // Computes and stores one item whose taps and halo are in buf.
-    static __device__ __forceinline__ void compute(const CtBatchProblem& pr, int tile, const float* buf)
+    static __device__ __noinline__ void compute(const CtBatchProblem& pr, int tile, const float* buf)
     {
         const int tid = threadIdx.x;
         const float* taps = buf;
