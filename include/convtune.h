@@ -324,7 +324,14 @@ CT_API ct_status ct_table_analyze(const ct_table* t, const ct_space* s, double f
  * problems; the default objective is the performance portability PP of Eq. 2
  * over the bucket's shapes (harmonic mean of the per-shape efficiencies of
  * Eq. 3), the alternative the bucket's summed time.  Results are bit-identical
- * to ct_conv2d on each problem. */
+ * to ct_conv2d on each problem.
+ *
+ * Each item's input halo and filter taps reach shared memory by tensor-memory
+ * copies (one 2D tensor map per problem, encoded at create for the bucket's
+ * tile); a tile's halo box is at most 256 x 256 elements, and a problem spans
+ * at most 65535 tiles along each side (otherwise CT_ERR_UNSUPPORTED).  A block
+ * that waits more than about two seconds for its copies gives up, records the
+ * failure in the plan's error word and exits; ct_batch_check reports it. */
 
 typedef struct {
     const void* d_image;   /* in_h x in_pitch elements of the batch dtype (caller-owned, kept alive) */
@@ -371,6 +378,11 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
 /* Runs the planned batch once on `stream` (one graph launch; asynchronous).
  * Runs of one plan must not overlap: they share its work counter. */
 CT_API ct_status ct_batch_run(ct_batch* b, void* stream);
+/* Reads the plan's error word (synchronously; call it after the runs have
+ * completed): CT_OK, or CT_ERR_TIMEOUT when a block of an earlier run gave up
+ * waiting for its input copies (its outputs are then incomplete).  The word is
+ * sticky for the life of the plan. */
+CT_API ct_status ct_batch_check(const ct_batch* b);
 CT_API ct_status ct_batch_info_get(const ct_batch* b, ct_batch_info* out);
 /* Bucket k: its filter size, number of problems, tile configuration and the
  * PP score (Eq. 2) of that configuration over the bucket's measured shapes

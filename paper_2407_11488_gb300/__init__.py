@@ -159,6 +159,7 @@ _SIGS = {
     "ct_table_analyze": (i32, [vp, vp, dbl, P(dbl), i32, P(Analysis)]),
     "ct_batch_create": (i32, [P(BatchItem), i32, P(BatchOpts), P(vp)]),
     "ct_batch_run": (i32, [vp, vp]),
+    "ct_batch_check": (i32, [vp]),
     "ct_batch_info_get": (i32, [vp, P(BatchInfo)]),
     "ct_batch_bucket": (i32, [vp, i32, P(i32), P(i32), P(i32), P(BucketConfig), P(dbl)]),
     "ct_batch_item_bucket": (i32, [vp, i32]),
@@ -554,6 +555,11 @@ class Batch:
 
     def run(self, stream=None):
         _check(_load().ct_batch_run(self.handle, _stream_ptr(stream)))
+
+    def check(self):
+        """Raises CTError(CT_ERR_TIMEOUT) when a block of an earlier run gave
+        up waiting for its input copies; call after the runs completed."""
+        _check(_load().ct_batch_check(self.handle))
 
     def info(self) -> dict:
         i = BatchInfo()

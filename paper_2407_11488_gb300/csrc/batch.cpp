@@ -2,6 +2,9 @@
 // the persistent launch and its CUDA graph.
 #include "batch_internal.hpp"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -22,9 +25,9 @@ std::vector<std::string> batch_options(int threads, int dtype, const std::vector
     def("CT_DTYPE", dtype);
     def("CT_NB", (int)b.size());
     def("CT_MINB", kMinBlocks);
-    int64_t buf = 4;
-    for (const auto& d : b) buf = std::max(buf, bucket_buf_floats(threads, d.cfg, d.fw, d.fh));
-    def("CT_BUF_FLOATS", (int)buf);
+    int64_t buf = 128;
+    for (const auto& d : b) buf = std::max(buf, bucket_buf_bytes(threads, d.cfg, d.fw, d.fh, dtype));
+    def("CT_BUF_BYTES", (int)buf);
     for (size_t k = 0; k < b.size(); ++k) {
         const std::string p = "CT_B" + std::to_string(k) + "_";
         def(p + "BX", b[k].cfg.bx);
@@ -54,9 +57,38 @@ VariantPtr compile_batch(int threads, int dtype, const std::vector<BucketDesc>& 
     VariantPtr v = compile_source(kBatchSource, sizeof kBatchSource, "batch.cu", batch_options(threads, dtype, b),
                                   "ct_corr2d_batch", dir);
     int64_t sm = 0;
-    for (const auto& d : b) sm = std::max(sm, bucket_smem(threads, d.cfg, d.fw, d.fh));
+    for (const auto& d : b) sm = std::max(sm, bucket_smem(threads, d.cfg, d.fw, d.fh, dtype));
     v->smem = sm;
     return v;
+}
+
+ct_status encode_halo_map(void* map, const void* d_image, int dtype, int64_t in_w, int64_t in_h, int64_t in_pitch,
+                          int64_t box_w, int64_t box_h)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode) return fail(CT_ERR_CUDA, "the driver offers no cuTensorMapEncodeTiled");
+    const cuuint64_t dims[2] = {(cuuint64_t)in_w, (cuuint64_t)in_h};
+    const cuuint64_t strides[1] = {(cuuint64_t)(in_pitch * elem_size(dtype))};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r =
+        encode(static_cast<CUtensorMap*>(map),
+               dtype == CT_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+               const_cast<void*>(d_image), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(CT_ERR_INVALID_ARG, "cuTensorMapEncodeTiled failed (%d) for a %lldx%lld image, box %lldx%lld",
+                    (int)r, (long long)in_w, (long long)in_h, (long long)box_w, (long long)box_h);
+    return CT_OK;
 }
 
 ct_status launch_batch(Variant& v, int grid, int threads, const DevParams& prm, cudaStream_t s)
@@ -109,6 +141,7 @@ struct ct_batch {
     void* d_probs = nullptr;
     void* d_work = nullptr;
     float* d_filters = nullptr;
+    void* d_tmaps = nullptr;
     unsigned* d_counter = nullptr;
     int64_t n_work = 0;
     int grid = 0;
@@ -120,6 +153,7 @@ struct ct_batch {
         if (d_probs) cudaFree(d_probs);
         if (d_work) cudaFree(d_work);
         if (d_filters) cudaFree(d_filters);
+        if (d_tmaps) cudaFree(d_tmaps);
         if (d_counter) cudaFree(d_counter);
     }
 };
@@ -158,10 +192,23 @@ DevProblem dev_problem(const ct_batch& B, int i, int bucket, const TileCfg& c)
     return d;
 }
 
+// Tensor map of item i's image for the halo box of tile configuration c
+// (all zero for an empty item, which has no tiles).
+ct_status item_map(const ct_batch& B, int i, const TileCfg& c, unsigned char* map)
+{
+    const ct_batch_item& it = B.items[(size_t)i];
+    memset(map, 0, kTensorMapBytes);
+    if (it.out_w == 0 || it.out_h == 0) return CT_OK;
+    return encode_halo_map(map, it.d_image, B.dtype, it.out_w + it.filter_w - 1, it.out_h + it.filter_h - 1,
+                           it.in_pitch, halo_box_w(B.threads, c, it.filter_w, B.dtype),
+                           halo_box_h(B.threads, c, it.filter_h));
+}
+
 // Candidate tiles of one bucket: block width, register tile, row-loop
-// unrolling; the two item buffers must leave room for min_blocks blocks per
-// SM, and a fully unrolled body stays below ~6k FMAs (instruction cache).
-std::vector<TileCfg> bucket_candidates(int threads, int fw, int fh, int smem_limit, int min_blocks)
+// unrolling; the halo box must suit a tensor copy, the two item buffers must
+// leave room for min_blocks blocks per SM, and a fully unrolled body stays
+// below ~6k FMAs (instruction cache).
+std::vector<TileCfg> bucket_candidates(int threads, int fw, int fh, int dtype, int smem_limit, int min_blocks)
 {
     std::vector<TileCfg> out;
     const int64_t cap = std::min<int64_t>(smem_limit, (int64_t)kSmemPerSM / std::max(1, min_blocks) - 1024);
@@ -171,13 +218,12 @@ std::vector<TileCfg> bucket_candidates(int threads, int fw, int fh, int smem_lim
             for (int ty : {1, 2, 4, 8})
                 for (int un : {0, 1}) {
                     TileCfg c{bx, tx, ty, un};
-                    if ((bx * tx) % 4) continue;
-                    if (bucket_smem(threads, c, fw, fh) > cap) continue;
+                    if (!halo_box_ok(threads, c, fw, fh, dtype)) continue;
+                    if (bucket_smem(threads, c, fw, fh, dtype) > cap) continue;
                     if (un && (int64_t)tx * ty * fw * (fh + ty - 1) > 6144) continue;
                     out.push_back(c);
                 }
     }
-    if (out.empty()) out.push_back(TileCfg{std::min(32, threads), 4, 1, 0});
     return out;
 }
 
@@ -186,8 +232,10 @@ std::vector<TileCfg> bucket_candidates(int threads, int fw, int fh, int smem_lim
 ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o, CompilePool& pool,
                       cudaStream_t s, int smem_limit)
 {
-    std::vector<TileCfg> cand = bucket_candidates(B.threads, bk.fw, bk.fh, smem_limit, kMinBlocks);
-    if (cand.empty()) return fail(CT_ERR_INVALID_CONFIG, "no tile fits shared memory for filter %dx%d", bk.fw, bk.fh);
+    std::vector<TileCfg> cand = bucket_candidates(B.threads, bk.fw, bk.fh, B.dtype, smem_limit, kMinBlocks);
+    if (cand.empty())
+        return fail(CT_ERR_INVALID_CONFIG, "no tile fits shared memory and the tensor copy for filter %dx%d", bk.fw,
+                    bk.fh);
     // sample of problems: sorted by size, evenly spaced, always the extremes
     std::vector<int> its = bk.items;
     std::sort(its.begin(), its.end(), [&](int a, int b) {
@@ -206,6 +254,17 @@ ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o,
         for (size_t k = 0; k < cap; ++k) sample.push_back(its[k * (its.size() - 1) / (cap - 1)]);
         sample.erase(std::unique(sample.begin(), sample.end()), sample.end());
     }
+    cand.erase(std::remove_if(cand.begin(), cand.end(),
+                              [&](const TileCfg& c) {
+                                  for (int i : sample)
+                                      if (!tile_grid_ok(B.items[(size_t)i].out_w, B.items[(size_t)i].out_h,
+                                                        tile_w(B.threads, c), tile_h(B.threads, c)))
+                                          return true;
+                                  return false;
+                              }),
+               cand.end());
+    if (cand.empty()) return fail(CT_ERR_UNSUPPORTED, "no tile keeps the bucket's problems within %lld tiles a side",
+                                  (long long)kMaxTilesPerSide);
     // compile all candidates in parallel
     std::vector<std::shared_future<VariantPtr>> futs;
     std::vector<uint64_t> keys;
@@ -222,6 +281,7 @@ ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o,
         for (int i : sample) max_tiles = std::max(max_tiles, tiles_of(B.items[(size_t)i], B.threads, c));
     void* d_prob = nullptr;
     void* d_work = nullptr;
+    void* d_map = nullptr;
     unsigned* d_cnt = nullptr;
     cudaEvent_t ev[2];
     cudaEventCreate(&ev[0]);
@@ -230,6 +290,7 @@ ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o,
         cudaStreamSynchronize(s);
         if (d_prob) cudaFree(d_prob);
         if (d_work) cudaFree(d_work);
+        if (d_map) cudaFree(d_map);
         if (d_cnt) cudaFree(d_cnt);
         cudaEventDestroy(ev[0]);
         cudaEventDestroy(ev[1]);
@@ -238,10 +299,13 @@ ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o,
     cudaError_t e;
     if ((e = cudaMalloc(&d_prob, sizeof(DevProblem))) != cudaSuccess ||
         (e = cudaMalloc(&d_work, (size_t)max_tiles * sizeof(WorkItem))) != cudaSuccess ||
-        (e = cudaMalloc((void**)&d_cnt, sizeof(unsigned))) != cudaSuccess) {
+        (e = cudaMalloc(&d_map, kTensorMapBytes)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&d_cnt, kCounterWords * sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMemsetAsync(d_cnt, 0, kCounterWords * sizeof(unsigned), s)) != cudaSuccess) {
         cleanup();
         return cuda_fail(e, "cudaMalloc(batch tuning scratch)");
     }
+    alignas(64) unsigned char map[kTensorMapBytes];
     const size_t nc = cand.size(), ni = sample.size();
     std::vector<double> t((size_t)(nc * ni), std::numeric_limits<double>::infinity());
     std::vector<WorkItem> work;
@@ -251,15 +315,21 @@ ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o,
         for (size_t ii = 0; ii < ni; ++ii) {
             const int item = sample[ii];
             const DevProblem dp = dev_problem(B, item, 0, cand[ci]);
-            const int64_t nt = tiles_of(B.items[(size_t)item], B.threads, cand[ci]);
+            ct_status st = item_map(B, item, cand[ci], map);
+            if (st != CT_OK) {
+                cleanup();
+                return st;
+            }
+            int64_t tx = 0;
+            const int64_t nt = tiles_of(B.items[(size_t)item], B.threads, cand[ci], &tx);
             work.resize((size_t)nt);
-            for (int64_t k = 0; k < nt; ++k) work[(size_t)k] = WorkItem{0u, (uint32_t)k};
+            for (int64_t k = 0; k < nt; ++k) work[(size_t)k] = work_item(0u, k, tx);
             cudaMemcpyAsync(d_prob, &dp, sizeof dp, cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(d_work, work.data(), (size_t)nt * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
-            ct_status st = load_variant(*v);
-            if (st != CT_OK) break;
+            cudaMemcpyAsync(d_map, map, kTensorMapBytes, cudaMemcpyHostToDevice, s);
+            if ((st = load_variant(*v)) != CT_OK) break;
             const int grid = occupancy_grid(*v, B.threads, o.blocks_per_sm, nt);
-            DevParams prm{d_prob, d_work, B.d_filters, d_cnt, (int32_t)nt, 0};
+            DevParams prm{d_prob, d_work, B.d_filters, d_map, d_cnt, (int32_t)nt, 0};
             std::vector<float> ms;
             bool ok = true;
             for (int r = 0; r < 4 && ok; ++r) {
@@ -418,7 +488,12 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
             } else {
                 bk.cfg = TileCfg{32, 4, 4, 0};
                 if (threads % 32) bk.cfg.bx = 16;
-                while (bucket_smem(threads, bk.cfg, bk.fw, bk.fh) > smem_limit && bk.cfg.ty > 1) bk.cfg.ty /= 2;
+                while ((bucket_smem(threads, bk.cfg, bk.fw, bk.fh, o.dtype) > smem_limit ||
+                        !halo_box_ok(threads, bk.cfg, bk.fw, bk.fh, o.dtype)) &&
+                       bk.cfg.ty > 1)
+                    bk.cfg.ty /= 2;
+                if (!halo_box_ok(threads, bk.cfg, bk.fw, bk.fh, o.dtype))
+                    return fail(CT_ERR_UNSUPPORTED, "no default tile suits a tensor copy with %d threads", threads);
             }
         }
     }
@@ -431,11 +506,15 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
     if (B->module->status != CT_OK) return fail(CT_ERR_COMPILE, "%s", B->module->error.c_str());
     if (B->module->smem > smem_limit) return fail(CT_ERR_INVALID_CONFIG, "batch kernel needs too much shared memory");
     if ((st = load_variant(*B->module)) != CT_OK) return st;   // also fills in the register count
-    // problem table and work list: most expensive tiles first
+    // problem table, tensor maps and work list: most expensive tiles first
     std::vector<DevProblem> probs;
+    std::vector<unsigned char> maps((size_t)n * kTensorMapBytes);
     for (int i = 0; i < n; ++i) {
         const int b = B->item_bucket[(size_t)i];
         probs.push_back(dev_problem(*B, i, b, B->buckets[(size_t)b].cfg));
+        alignas(64) unsigned char map[kTensorMapBytes];
+        if ((st = item_map(*B, i, B->buckets[(size_t)b].cfg, map)) != CT_OK) return st;
+        memcpy(maps.data() + (size_t)i * kTensorMapBytes, map, kTensorMapBytes);
     }
     std::vector<int> border(B->buckets.size());
     std::iota(border.begin(), border.end(), 0);
@@ -451,23 +530,31 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
             return (int64_t)items[a].out_w * items[a].out_h > (int64_t)items[c].out_w * items[c].out_h;
         });
         for (int i : its) {
-            const int64_t nt = tiles_of(items[i], threads, B->buckets[(size_t)b].cfg);
-            for (int64_t k = 0; k < nt; ++k) work.push_back(WorkItem{(uint32_t)i, (uint32_t)k});
+            const TileCfg& c = B->buckets[(size_t)b].cfg;
+            if (!tile_grid_ok(items[i].out_w, items[i].out_h, tile_w(threads, c), tile_h(threads, c)))
+                return fail(CT_ERR_UNSUPPORTED, "batch item %d: more than %lld tiles along one side", i,
+                            (long long)kMaxTilesPerSide);
+            int64_t tx = 0;
+            const int64_t nt = tiles_of(items[i], threads, c, &tx);
+            for (int64_t k = 0; k < nt; ++k) work.push_back(work_item((uint32_t)i, k, tx));
         }
     }
     if (work.size() > (size_t)0x7fffffff) return fail(CT_ERR_UNSUPPORTED, "too many tiles in one batch");
     B->n_work = (int64_t)work.size();
     if ((e = cudaMalloc(&B->d_probs, probs.size() * sizeof(DevProblem))) != cudaSuccess ||
         (e = cudaMalloc(&B->d_work, std::max<size_t>(1, work.size()) * sizeof(WorkItem))) != cudaSuccess ||
-        (e = cudaMalloc((void**)&B->d_counter, sizeof(unsigned))) != cudaSuccess)
+        (e = cudaMalloc(&B->d_tmaps, maps.size())) != cudaSuccess ||
+        (e = cudaMalloc((void**)&B->d_counter, kCounterWords * sizeof(unsigned))) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(batch tables)");
+    cudaMemsetAsync(B->d_counter, 0, kCounterWords * sizeof(unsigned), s);
     cudaMemcpyAsync(B->d_probs, probs.data(), probs.size() * sizeof(DevProblem), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(B->d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice, s);
     if (!work.empty())
         cudaMemcpyAsync(B->d_work, work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "upload batch tables");
     B->grid = occupancy_grid(*B->module, threads, o.blocks_per_sm, std::max<int64_t>(1, B->n_work));
     // capture: counter reset + the persistent launch
-    DevParams prm{B->d_probs, B->d_work, B->d_filters, B->d_counter, (int32_t)B->n_work, 0};
+    DevParams prm{B->d_probs, B->d_work, B->d_filters, B->d_tmaps, B->d_counter, (int32_t)B->n_work, 0};
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamBeginCapture");
@@ -500,6 +587,16 @@ CT_API ct_status ct_batch_run(ct_batch* b, void* stream)
     if (!b || !b->exec) return fail(CT_ERR_INVALID_ARG, "batch is NULL");
     cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch(batch)");
+    return CT_OK;
+}
+
+CT_API ct_status ct_batch_check(const ct_batch* b)
+{
+    if (!b || !b->d_counter) return fail(CT_ERR_INVALID_ARG, "batch is NULL");
+    unsigned words[kCounterWords] = {};
+    const cudaError_t e = cudaMemcpy(words, b->d_counter, sizeof words, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read the batch status");
+    if (words[1] & 1u) return fail(CT_ERR_TIMEOUT, "a block of an earlier run gave up waiting for its input copies");
     return CT_OK;
 }
 

@@ -27,14 +27,28 @@ struct DevParams {
     const void* probs;
     const void* work;
     const float* filters;
-    unsigned* counter;
+    const void* tmaps;   // one 128-byte tensor map per problem
+    unsigned* counter;   // kCounterWords words: next work item, error bits
     int32_t n_work;
     int32_t pad;
 };
-static_assert(sizeof(DevParams) == 40, "DevParams layout");
+static_assert(sizeof(DevParams) == 48, "DevParams layout");
+constexpr int kCounterWords = 2;
+constexpr size_t kTensorMapBytes = 128;
+// One tile of one problem; the tile is (row << 16) | column, so the kernel
+// places it without a division.
 struct WorkItem {
     uint32_t problem, tile;
 };
+constexpr int64_t kMaxTilesPerSide = 65535;
+inline WorkItem work_item(uint32_t problem, int64_t k, int64_t tiles_x)
+{
+    return WorkItem{problem, (uint32_t)(((k / tiles_x) << 16) | (k % tiles_x))};
+}
+inline bool tile_grid_ok(int64_t out_w, int64_t out_h, int64_t tw, int64_t th)
+{
+    return (out_w + tw - 1) / tw <= kMaxTilesPerSide && (out_h + th - 1) / th <= kMaxTilesPerSide;
+}
 
 constexpr int64_t kSmemPerSM = 233472;   // shared memory per SM usable by blocks
 constexpr int kMinBlocks = 4;            // resident blocks per SM the batch kernel is built for
@@ -47,19 +61,36 @@ struct BucketDesc {
 inline int64_t tile_w(int threads, const TileCfg& c) { (void)threads; return (int64_t)c.bx * c.tx; }
 inline int64_t tile_h(int threads, const TileCfg& c) { return (int64_t)(threads / c.bx) * c.ty; }
 
-// floats of one item buffer (taps + halo), a multiple of 4
-inline int64_t bucket_buf_floats(int threads, const TileCfg& c, int fw, int fh)
+// The halo box of a tile: the tile plus the filter's apron, its width rounded
+// up to 16 bytes; at most 256 elements per side (the tensor-copy limit).
+inline int64_t halo_box_w(int threads, const TileCfg& c, int fw, int dtype)
 {
-    const int64_t hh = tile_h(threads, c) + fh - 1;
-    const int64_t sw = round_up(tile_w(threads, c) + fw - 1, 4);
-    return round_up(fh * round_up(fw, 4) + hh * sw, 4);
+    return round_up(tile_w(threads, c) + fw - 1, 16 / elem_size(dtype));
+}
+inline int64_t halo_box_h(int threads, const TileCfg& c, int fh) { return tile_h(threads, c) + fh - 1; }
+inline bool halo_box_ok(int threads, const TileCfg& c, int fw, int fh, int dtype)
+{
+    return halo_box_w(threads, c, fw, dtype) <= 256 && halo_box_h(threads, c, fh) <= 256 &&
+           tile_w(threads, c) % 16 == 0;
 }
 
-// dynamic shared memory of the kernel: two item buffers
-inline int64_t bucket_smem(int threads, const TileCfg& c, int fw, int fh)
+// bytes of one item buffer (halo box, then taps), a multiple of 128
+inline int64_t bucket_buf_bytes(int threads, const TileCfg& c, int fw, int fh, int dtype)
 {
-    return 2 * 4 * bucket_buf_floats(threads, c, fw, fh);
+    const int64_t halo = halo_box_w(threads, c, fw, dtype) * halo_box_h(threads, c, fh) * elem_size(dtype);
+    return round_up(round_up(halo, 16) + (int64_t)fh * round_up(fw, 4) * 4, 128);
 }
+
+// dynamic shared memory of the kernel: two item buffers plus alignment slack
+inline int64_t bucket_smem(int threads, const TileCfg& c, int fw, int fh, int dtype)
+{
+    return 2 * bucket_buf_bytes(threads, c, fw, fh, dtype) + 128;
+}
+
+// Writes the 128-byte tensor map of an image (in_w x in_h elements, rows
+// in_pitch elements apart, 16-byte aligned) whose box is the halo of one tile.
+ct_status encode_halo_map(void* map, const void* d_image, int dtype, int64_t in_w, int64_t in_h, int64_t in_pitch,
+                          int64_t box_w, int64_t box_h);
 
 std::vector<std::string> batch_options(int threads, int dtype, const std::vector<BucketDesc>& b);
 

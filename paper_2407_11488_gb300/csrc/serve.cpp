@@ -116,6 +116,7 @@ struct Launch {
     size_t tab_off = 0, tab_bytes = 0;
     unsigned char* staging = nullptr;
     size_t staging_bytes = 0;
+    ct_status launched = CT_OK;   // status of starting the kernel
 };
 
 double now_s()
@@ -198,14 +199,18 @@ bool ct_server::step_locked()
         const cudaError_t e = cudaEventQuery(L.done);
         if (e == cudaErrorNotReady) continue;
         const double t = now_s();
+        unsigned kerr = 0;
+        memcpy(&kerr, L.staging + 4, 4);
+        const bool good = e == cudaSuccess && kerr == 0 && L.launched == CT_OK;
+        const ct_status why = e != cudaSuccess ? CT_ERR_CUDA : (L.launched != CT_OK ? L.launched : CT_ERR_TIMEOUT);
         for (auto& r : L.reqs) {
-            r->state = e == cudaSuccess ? RState::Done : RState::Failed;
-            r->status = e == cudaSuccess ? CT_OK : CT_ERR_CUDA;
+            r->state = good ? RState::Done : RState::Failed;
+            r->status = good ? CT_OK : why;
             r->t_done = t;
             if (r->own_image) arena.release(r->img_off, r->img_bytes);
             else images[r->rq.image_id].users--;
             arena.release(r->out_off, r->out_bytes);
-            if (e == cudaSuccess) {
+            if (good) {
                 lat_ms.push_back(1e3 * (t - r->t_submit));
                 completed++;
                 flops += 2.0 * r->rq.out_w * (double)r->rq.out_h * r->rq.filter_w * r->rq.filter_h;
@@ -293,7 +298,8 @@ bool ct_server::launch_locked(Launch& L)
         return a * b;
     };
     auto bytes_for = [&](size_t np, size_t nt, int64_t nw) {
-        return 256 + np * sizeof(DevProblem) + ((nt * 4 + 255) / 256) * 256 + (size_t)nw * sizeof(WorkItem) + 256;
+        return 256 + np * (kTensorMapBytes + sizeof(DevProblem)) + ((nt * 4 + 255) / 256) * 256 +
+               (size_t)nw * sizeof(WorkItem) + 256;
     };
     while (!ready.empty() && (int)take.size() < o.max_batch) {
         const Request& r = *ready.front();
@@ -321,11 +327,13 @@ bool ct_server::launch_locked(Launch& L)
         for (auto it = take.rbegin(); it != take.rend(); ++it) ready.push_front(*it);
         return false;
     }
-    // host tables: [counter 256][problems][filters][work]
+    // host tables: [counter and error word, 256][tensor maps][problems][filters][work]
     unsigned char* st = L.staging;
     memset(st, 0, 256);
-    DevProblem* probs = reinterpret_cast<DevProblem*>(st + 256);
-    const size_t off_f = 256 + take.size() * sizeof(DevProblem);
+    unsigned char* maps = st + 256;
+    const size_t off_p = 256 + take.size() * kTensorMapBytes;
+    DevProblem* probs = reinterpret_cast<DevProblem*>(st + off_p);
+    const size_t off_f = off_p + take.size() * sizeof(DevProblem);
     float* filt = reinterpret_cast<float*>(st + off_f);
     const size_t off_w = off_f + ((n_taps * 4 + 255) / 256) * 256;
     WorkItem* work = reinterpret_cast<WorkItem*>(st + off_w);
@@ -348,20 +356,31 @@ bool ct_server::launch_locked(Launch& L)
         d.tiles_x = (int32_t)tx;
         d.filt_off = (int32_t)toff;
         d.pad = 0;
+        const TileCfg& c = buckets[(size_t)r.bucket].cfg;
+        const ct_status ms = encode_halo_map(maps + i * kTensorMapBytes, r.d_image, o.dtype, d.in_w, d.in_h,
+                                             r.in_pitch, halo_box_w(threads, c, r.rq.filter_w, o.dtype),
+                                             halo_box_h(threads, c, r.rq.filter_h));
+        if (ms != CT_OK) {
+            fatal = ms;
+            fatal_msg = last_error();
+        }
         memcpy(filt + toff, r.taps.data(), r.taps.size() * 4);
         toff += r.taps.size();
-        for (int64_t k = 0; k < nt; ++k) work[w++] = WorkItem{(uint32_t)i, (uint32_t)k};
+        for (int64_t k = 0; k < nt; ++k) work[w++] = work_item((uint32_t)i, k, tx);
     }
     unsigned char* dt = base + tab_off;
     cudaMemcpyAsync(dt, st, tab_bytes, cudaMemcpyHostToDevice, L.stream);
-    DevParams prm{dt + 256, dt + off_w, reinterpret_cast<const float*>(dt + off_f),
+    DevParams prm{dt + off_p, dt + off_w, reinterpret_cast<const float*>(dt + off_f), dt + 256,
                   reinterpret_cast<unsigned*>(dt), (int32_t)n_work, 0};
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(max_grid, n_work));
-    ct_status s = launch_batch(*module, grid, threads, prm, L.stream);
-    if (s != CT_OK) {
+    ct_status s = fatal == CT_OK ? launch_batch(*module, grid, threads, prm, L.stream) : (ct_status)fatal;
+    if (s != CT_OK && fatal == CT_OK) {
         fatal = s;
         fatal_msg = last_error();
     }
+    L.launched = s;
+    // the kernel's error word comes back into the (already uploaded) staging buffer
+    cudaMemcpyAsync(L.staging + 4, dt + 4, 4, cudaMemcpyDeviceToHost, L.stream);
     for (auto& r : take) {
         cudaMemcpy2DAsync((void*)r->rq.h_out, (size_t)r->rq.out_pitch * 4, base + r->out_off,
                           (size_t)r->out_dpitch * 4, (size_t)r->rq.out_w * 4, (size_t)r->rq.out_h,
@@ -539,6 +558,12 @@ CT_API ct_status ct_server_submit(ct_server* s, const ct_request* rq, uint64_t* 
                     rq->filter_h, s->o.filter_min, s->o.filter_max);
     if (rq->out_w <= 0 || rq->out_h <= 0) return fail(CT_ERR_INVALID_ARG, "empty request");
     if (rq->out_pitch < rq->out_w) return fail(CT_ERR_INVALID_ARG, "out_pitch < out_w");
+    {
+        const TileCfg& c = s->buckets[(size_t)b].cfg;
+        if (!tile_grid_ok(rq->out_w, rq->out_h, tile_w(s->threads, c), tile_h(s->threads, c)))
+            return fail(CT_ERR_UNSUPPORTED, "request of %dx%d outputs spans more than %lld tiles along one side",
+                        rq->out_w, rq->out_h, (long long)kMaxTilesPerSide);
+    }
     auto r = std::make_shared<Request>();
     r->rq = *rq;
     r->bucket = b;

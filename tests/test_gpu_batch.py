@@ -1,7 +1,11 @@
 """GPU tests of the batched persistent path (many uneven correlations in one
 launch): every problem matches the FP64 oracle within 1e-5 * sum|in*f| and is
 bit-identical to the single-problem kernel; guard bands stay intact; the
-graph can be replayed; bucket tuning reports a valid PP score."""
+graph can be replayed; bucket tuning reports a valid PP score; the plan's
+error word stays clear, and a wait that cannot complete gives up and is
+reported."""
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -53,6 +57,7 @@ def test_batch_matches_oracle_and_single_kernel(ctlib, cuda_device, tune):
     for rep in range(2):       # the graph is replayable
         b.run()
         torch.cuda.synchronize()
+        b.check()
         for (img, f, d, out, ow, oh, fw, fh) in probs:
             assert _guards_ok(out, ow, oh), (ow, oh, fw, fh)
             got = out[:oh, :ow].cpu().numpy()
@@ -78,6 +83,7 @@ def test_batch_bf16(ctlib, cuda_device):
     b = ctlib.Batch([(d, f, out, ow + fw - 1) for (_, f, d, out, ow, oh, fw, fh) in probs], tune=False)
     b.run()
     torch.cuda.synchronize()
+    b.check()
     for (img, f, d, out, ow, oh, fw, fh) in probs:
         ib = torch.from_numpy(img).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
         fb = f.view(torch.int16).numpy().view(np.uint16)
@@ -99,8 +105,49 @@ def test_batch_workload_sampled(ctlib, cuda_device):
                     max_tune_items=3)
     b.run()
     torch.cuda.synchronize()
+    b.check()
     for k, (img, f, d, out, side, fs) in enumerate(probs):
         xs, ys = synthetic.sample_points(k, side, side, 64)
         ref, S = oracle.corr2d_points(img, f, xs, ys)
         got = out.cpu().numpy()[ys, xs].astype(np.float64)
         assert np.all(np.abs(got - ref) <= 1e-5 * S), (k, side, fs)
+
+
+def test_tile_grid_limit(ctlib, cuda_device):
+    """A problem wider than 65535 tiles of any candidate tile is refused at
+    plan time (CT_ERR_UNSUPPORTED), tuned or not; no kernel runs."""
+    ow = 1 << 24
+    img = torch.zeros((1, ow), device=cuda_device)
+    out = torch.empty((1, ow), device=cuda_device)
+    f = np.ones((1, 1), np.float32)
+    for tune in (True, False):
+        with pytest.raises(ctlib.CTError) as e:
+            ctlib.Batch([(img, f, out, ow)], tune=tune)
+        assert e.value.status == -8
+
+
+def test_wait_timeout_is_reported(ctlib, cuda_device, monkeypatch):
+    """With the kernel built to expect 16 bytes per item more than its copies
+    deliver, no wait can complete: every block gives up after its bounded
+    wait, the error word reports CT_ERR_TIMEOUT, and the context stays usable
+    for a normal batch afterwards."""
+    probs = _make([(64, 64, 3, 3)], 9, cuda_device)
+    items = [(d, f, out, ow + fw - 1) for (_, f, d, out, ow, oh, fw, fh) in probs]
+    monkeypatch.setenv("CONVTUNE_NVRTC_EXTRA", "-DCT_TEST_EXTRA_TX=16")
+    bad = ctlib.Batch(items, tune=False)
+    monkeypatch.delenv("CONVTUNE_NVRTC_EXTRA")
+    t0 = time.time()
+    bad.run()
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 30.0
+    with pytest.raises(ctlib.CTError) as e:
+        bad.check()
+    assert e.value.status == -7
+    del bad
+    good = ctlib.Batch(items, tune=False)
+    good.run()
+    torch.cuda.synchronize()
+    good.check()
+    img, f, d, out, ow, oh, fw, fh = probs[0]
+    ref, S = oracle.corr2d_f64(img, f, ow, oh)
+    assert_parity(out[:oh, :ow].cpu().numpy(), ref, S, "batch after a timed-out run")
