@@ -12,7 +12,9 @@ Timed region: W untimed steps, then K steps, each bracketed by CUDA events on
 the launching stream, with L2 overwritten (a 2x-L2 buffer) between steps and
 outside the events; barrier + synchronize on both sides; max over ranks.
 e2e: the same metric through the host-buffer entry point (pinned host image
-copied in, result copied out, every step).  One JSON line on rank 0.
+copied in, result copied out, every step), with the floor the host link sets
+for those bytes (link_floor_ms: both copies alone, concurrently, on the copy
+engines).  One JSON line on rank 0.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--strategy random|anneal|brute]
     python bench.py --impl reference ...   # the CPU oracle on the host cores
@@ -393,6 +395,29 @@ def run_ours(args):
         dones[1].synchronize()
         te = (time.perf_counter() - te0) / e_steps
     e2e_value = world * flops / te / 1e9
+
+    # the link's floor for the same bytes: the image in and the result out as
+    # two concurrent plain copies on the copy engines, best of 20
+    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    link_floor = float("inf")
+    for r in range(23):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_in, e_out = torch.cuda.Event(), torch.cuda.Event()
+        e0.record(stream)
+        s_in.wait_event(e0)
+        s_out.wait_event(e0)
+        with torch.cuda.stream(s_in):
+            d_imgs[1].copy_(h_img, non_blocking=True)
+            e_in.record(s_in)
+        with torch.cuda.stream(s_out):
+            h_outs[1].copy_(d_outs[1], non_blocking=True)
+            e_out.record(s_out)
+        stream.wait_event(e_in)
+        stream.wait_event(e_out)
+        e1.record(stream)
+        e1.synchronize()
+        if r >= 3:
+            link_floor = min(link_floor, e0.elapsed_time(e1))
     clocks.stop()
     clk = clocks.summary(tw0, tw1)
     if clk["samples"] == 0:
@@ -429,7 +454,8 @@ def run_ours(args):
                    for k, v in tuning.items()},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h_img.numel() * h_img.element_size()),
-                "d2h_bytes_per_step": int(h_out.numel() * 4), "ms_per_step": te * 1e3},
+                "d2h_bytes_per_step": int(h_out.numel() * 4), "ms_per_step": te * 1e3,
+                "link_floor_ms": link_floor, "frac_of_link_floor": link_floor / (te * 1e3)},
         "gpu_launches": args.steps,
         "clocks": clk,
         "device": info.name.decode(),

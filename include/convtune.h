@@ -144,12 +144,23 @@ CT_API ct_status ct_compile(const ct_problem* p, const ct_config* c, ct_variant_
 
 /* ---- the correlation ---------------------------------------------------- */
 
+/* Reads the current device's error word, which a ct_conv2d launch sets when
+ * its wait for its tensor copy gave up after about two seconds (that launch
+ * then stored nothing).  Synchronous: call it once the launches to check have
+ * completed.  CT_OK, or CT_ERR_TIMEOUT (and the word is cleared when clear is
+ * nonzero).  ct_tune checks the word after every configuration it times and
+ * records such a configuration as failed with CT_ERR_TIMEOUT. */
+CT_API ct_status ct_device_check(int32_t clear);
+
 /* out = correlate(image, filter) with configuration c, enqueued on stream.
  * d_image: in_h x in_pitch elements of p->dtype.  h_filter: filter_h x
  * filter_w row-major host array (float for CT_F32, raw bf16 bits uint16_t for
  * CT_BF16); it is copied into the launch before return.  d_out: out_h x
  * out_pitch floats.  Asynchronous with respect to the host; the first call
- * for a variant compiles and loads it (synchronously).  Errors:
+ * for a variant compiles and loads it (synchronously).  Variants that stage
+ * their halo in shared memory with a halo of at most 256 x 256 elements load
+ * it with one tensor copy (the image's tensor map travels in the launch);
+ * their wait for it is bounded (see ct_device_check).  Errors:
  * CT_ERR_INVALID_ARG / CT_ERR_INVALID_CONFIG (nothing enqueued),
  * CT_ERR_COMPILE, CT_ERR_LAUNCH, CT_ERR_CUDA, CT_ERR_UNSUPPORTED. */
 CT_API ct_status ct_conv2d(const ct_problem* p, const ct_config* c, const void* d_image,

@@ -140,6 +140,7 @@ _SIGS = {
     "ct_default_config": (i32, [P(Problem), P(Config)]),
     "ct_check_config": (i32, [P(Problem), P(Config), i32]),
     "ct_compile": (i32, [P(Problem), P(Config), P(VariantInfo)]),
+    "ct_device_check": (i32, [i32]),
     "ct_conv2d": (i32, [P(Problem), P(Config), vp, vp, vp, vp]),
     "ct_conv2d_host": (i32, [P(Problem), P(Config), vp, vp, vp, vp, vp, vp]),
     "ct_conv2d_host_pitched": (i32, [P(Problem), P(Config), vp, i64, vp, vp, i64, vp, vp, vp]),
@@ -221,6 +222,13 @@ def device_query() -> DeviceInfo:
     d = DeviceInfo()
     _check(_load().ct_device_query(ctypes.byref(d)))
     return d
+
+
+def device_check(clear: bool = True):
+    """Raises CTError(CT_ERR_TIMEOUT) when a ct_conv2d launch on the current
+    device gave up waiting for its input copy (call after the launches have
+    completed); clears the device's error word when ``clear``."""
+    _check(_load().ct_device_check(1 if clear else 0))
 
 
 def set_cache_dir(path):

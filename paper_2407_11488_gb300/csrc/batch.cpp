@@ -2,9 +2,6 @@
 // the persistent launch and its CUDA graph.
 #include "batch_internal.hpp"
 
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -62,34 +59,6 @@ VariantPtr compile_batch(int threads, int dtype, const std::vector<BucketDesc>& 
     return v;
 }
 
-ct_status encode_halo_map(void* map, const void* d_image, int dtype, int64_t in_w, int64_t in_h, int64_t in_pitch,
-                          int64_t box_w, int64_t box_h)
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
-        void* fn = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            fn = nullptr;
-        cudaGetLastError();
-        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }();
-    if (!encode) return fail(CT_ERR_CUDA, "the driver offers no cuTensorMapEncodeTiled");
-    const cuuint64_t dims[2] = {(cuuint64_t)in_w, (cuuint64_t)in_h};
-    const cuuint64_t strides[1] = {(cuuint64_t)(in_pitch * elem_size(dtype))};
-    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r =
-        encode(static_cast<CUtensorMap*>(map),
-               dtype == CT_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-               const_cast<void*>(d_image), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS)
-        return fail(CT_ERR_INVALID_ARG, "cuTensorMapEncodeTiled failed (%d) for a %lldx%lld image, box %lldx%lld",
-                    (int)r, (long long)in_w, (long long)in_h, (long long)box_w, (long long)box_h);
-    return CT_OK;
-}
 
 ct_status launch_batch(Variant& v, int grid, int threads, const DevParams& prm, cudaStream_t s)
 {
@@ -200,8 +169,8 @@ ct_status item_map(const ct_batch& B, int i, const TileCfg& c, unsigned char* ma
     memset(map, 0, kTensorMapBytes);
     if (it.out_w == 0 || it.out_h == 0) return CT_OK;
     return encode_halo_map(map, it.d_image, B.dtype, it.out_w + it.filter_w - 1, it.out_h + it.filter_h - 1,
-                           it.in_pitch, halo_box_w(B.threads, c, it.filter_w, B.dtype),
-                           halo_box_h(B.threads, c, it.filter_h));
+                           it.in_pitch, batch_box_w(B.threads, c, it.filter_w, B.dtype),
+                           batch_box_h(B.threads, c, it.filter_h));
 }
 
 // Candidate tiles of one bucket: block width, register tile, row-loop

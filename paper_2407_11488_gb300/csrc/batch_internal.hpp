@@ -34,7 +34,6 @@ struct DevParams {
 };
 static_assert(sizeof(DevParams) == 48, "DevParams layout");
 constexpr int kCounterWords = 2;
-constexpr size_t kTensorMapBytes = 128;
 // One tile of one problem; the tile is (row << 16) | column, so the kernel
 // places it without a division.
 struct WorkItem {
@@ -63,21 +62,21 @@ inline int64_t tile_h(int threads, const TileCfg& c) { return (int64_t)(threads 
 
 // The halo box of a tile: the tile plus the filter's apron, its width rounded
 // up to 16 bytes; at most 256 elements per side (the tensor-copy limit).
-inline int64_t halo_box_w(int threads, const TileCfg& c, int fw, int dtype)
+inline int64_t batch_box_w(int threads, const TileCfg& c, int fw, int dtype)
 {
     return round_up(tile_w(threads, c) + fw - 1, 16 / elem_size(dtype));
 }
-inline int64_t halo_box_h(int threads, const TileCfg& c, int fh) { return tile_h(threads, c) + fh - 1; }
+inline int64_t batch_box_h(int threads, const TileCfg& c, int fh) { return tile_h(threads, c) + fh - 1; }
 inline bool halo_box_ok(int threads, const TileCfg& c, int fw, int fh, int dtype)
 {
-    return halo_box_w(threads, c, fw, dtype) <= 256 && halo_box_h(threads, c, fh) <= 256 &&
+    return batch_box_w(threads, c, fw, dtype) <= 256 && batch_box_h(threads, c, fh) <= 256 &&
            tile_w(threads, c) % 16 == 0;
 }
 
 // bytes of one item buffer (halo box, then taps), a multiple of 128
 inline int64_t bucket_buf_bytes(int threads, const TileCfg& c, int fw, int fh, int dtype)
 {
-    const int64_t halo = halo_box_w(threads, c, fw, dtype) * halo_box_h(threads, c, fh) * elem_size(dtype);
+    const int64_t halo = batch_box_w(threads, c, fw, dtype) * batch_box_h(threads, c, fh) * elem_size(dtype);
     return round_up(round_up(halo, 16) + (int64_t)fh * round_up(fw, 4) * 4, 128);
 }
 
@@ -86,11 +85,6 @@ inline int64_t bucket_smem(int threads, const TileCfg& c, int fw, int fh, int dt
 {
     return 2 * bucket_buf_bytes(threads, c, fw, fh, dtype) + 128;
 }
-
-// Writes the 128-byte tensor map of an image (in_w x in_h elements, rows
-// in_pitch elements apart, 16-byte aligned) whose box is the halo of one tile.
-ct_status encode_halo_map(void* map, const void* d_image, int dtype, int64_t in_w, int64_t in_h, int64_t in_pitch,
-                          int64_t box_w, int64_t box_h);
 
 std::vector<std::string> batch_options(int threads, int dtype, const std::vector<BucketDesc>& b);
 

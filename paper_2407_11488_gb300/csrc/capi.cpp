@@ -89,6 +89,20 @@ CT_API ct_status ct_compile(const ct_problem* p, const ct_config* c, ct_variant_
     return CT_OK;
 }
 
+CT_API ct_status ct_device_check(int32_t clear)
+{
+    ct_status st = require_device();
+    if (st != CT_OK) return st;
+    unsigned* w = device_error_word();
+    if (!w) return fail(CT_ERR_CUDA, "no device error word");
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpy(&v, w, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read the device error word");
+    if (!(v & 1u)) return CT_OK;
+    if (clear && (e = cudaMemset(w, 0, 4)) != cudaSuccess) return cuda_fail(e, "clear the device error word");
+    return fail(CT_ERR_TIMEOUT, "a correlation launch gave up waiting for its input copy");
+}
+
 CT_API ct_status ct_conv2d(const ct_problem* p, const ct_config* c, const void* d_image, const void* h_filter,
                            float* d_out, void* stream)
 {

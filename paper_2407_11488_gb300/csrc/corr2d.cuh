@@ -19,8 +19,14 @@
 //   CT_SMEM        0: each thread reads its input window from global memory
 //                     (through L1);
 //                  1: the block stages its input tile plus halo in shared
-//                     memory with 16-byte vector loads, then reads windows
-//                     from there
+//                     memory, then reads windows from there
+//   CT_TMA         (chosen by the host for CT_SMEM = 1 when the halo box is
+//                  at most 256 x 256 elements) 1: one thread stages the halo
+//                  with a 2D tensor copy (the tensor map in the parameter
+//                  block; elements outside the image arrive as zeros) that
+//                  completes on an mbarrier; BF16 stays BF16 in shared memory
+//                  and is widened when a row enters registers.  0: every
+//                  thread copies 16-byte chunks
 //   CT_UNROLL      1: fully unrolled; input rows slide through a register
 //                     window and each row feeds every output row that uses it;
 //                  0: the loop over filter rows stays rolled
@@ -31,10 +37,20 @@
 // elements and make every row start on a 16-byte boundary; the image buffer
 // holds in_h full rows of in_pitch elements; the filter taps travel by value
 // in the kernel's parameter block (constant bank), so FFMAs take them as
-// uniform operands with no load instruction.
+// uniform operands with no load instruction.  A wait for the tensor copy
+// gives up after about two seconds: the block then sets bit 0 of the error
+// word, waits (again bounded) for the copy, and stores nothing.
 
 #ifndef CT_DTYPE
 #define CT_DTYPE 0
+#endif
+#ifndef CT_TMA
+#define CT_TMA 0
+#endif
+// Test hook: bytes expected on top of those the tensor copy delivers; a
+// nonzero value makes the wait run out.  0 in every normal build.
+#ifndef CT_TEST_EXTRA_TX
+#define CT_TEST_EXTRA_TX 0
 #endif
 
 #ifdef CT_INJECT_COMPILE_ERROR
@@ -50,13 +66,19 @@ typedef float ct_in_t;
 typedef unsigned short ct_in_t;
 #endif
 
+struct __align__(64) CtTensorMap {
+    unsigned long long q[16];
+};
+
 struct CtParams {
+    CtTensorMap tmap;   // the image's tensor map (CT_TMA variants; zero otherwise)
     const ct_in_t* in;
     float* out;
     ct_i64 in_pitch;
     ct_i64 out_pitch;
     int out_w, out_h;
     int in_w, in_h;
+    unsigned* err;      // error word
     float f[CT_FH * CT_FW];
 };
 
@@ -67,6 +89,8 @@ struct CtParams {
 #define CT_HALO_W (CT_TILE_W + CT_FW - 1)
 #define CT_HALO_H (CT_TILE_H + CT_FH - 1)
 #define CT_SW (((CT_HALO_W + 3) / 4) * 4)
+#define CT_ESZ (CT_DTYPE == 0 ? 4 : 2)
+#define CT_SWT (((CT_HALO_W + 16 / CT_ESZ - 1) / (16 / CT_ESZ)) * (16 / CT_ESZ))   // tensor-copy box width
 
 #if CT_TX % 4 == 0
 #define CT_VW 4
@@ -133,6 +157,63 @@ __device__ __forceinline__ void ct_row_global(float (&w)[CT_WWV], const CtParams
     }
 }
 
+#if CT_TMA
+__device__ __forceinline__ unsigned ct_sa(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool ct_bar_try_wait(unsigned long long* bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(ct_sa(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Waits for phase `parity` of bar; false after about two seconds.
+__device__ __forceinline__ bool ct_bar_wait(unsigned long long* bar, unsigned parity)
+{
+    if (ct_bar_try_wait(bar, parity)) return true;
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t0));
+    for (;;) {
+        if (ct_bar_try_wait(bar, parity)) return true;
+        asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+        if (t - t0 > 2000000000ull) return false;
+    }
+}
+
+// One input row of the thread's window from the tensor-copied halo (storage
+// dtype, CT_SWT elements per row), widened to FP32.
+__device__ __forceinline__ void ct_row_staged(float (&w)[CT_WWV], const ct_in_t* __restrict__ s)
+{
+#pragma unroll
+    for (int k = 0; k < CT_WWV; k += CT_VW) {
+#if CT_DTYPE == 0
+        if (CT_VW == 4) {
+            const float4 v = *reinterpret_cast<const float4*>(s + k);
+            w[k] = v.x; w[k + 1] = v.y; w[k + 2] = v.z; w[k + 3] = v.w;
+        } else if (CT_VW == 2) {
+            const float2 v = *reinterpret_cast<const float2*>(s + k);
+            w[k] = v.x; w[k + 1] = v.y;
+        } else {
+            w[k] = s[k];
+        }
+#else
+        if (CT_VW == 4) {
+            const uint2 v = *reinterpret_cast<const uint2*>(s + k);
+            w[k] = __uint_as_float(v.x << 16); w[k + 1] = __uint_as_float(v.x & 0xffff0000u);
+            w[k + 2] = __uint_as_float(v.y << 16); w[k + 3] = __uint_as_float(v.y & 0xffff0000u);
+        } else if (CT_VW == 2) {
+            const ct_u32 v = *reinterpret_cast<const ct_u32*>(s + k);
+            w[k] = __uint_as_float(v << 16); w[k + 1] = __uint_as_float(v & 0xffff0000u);
+        } else {
+            w[k] = ct_bf16(s[k]);
+        }
+#endif
+    }
+}
+#endif
+
 __device__ __forceinline__ void ct_row_shared(float (&w)[CT_WWV], const float* __restrict__ s)
 {
 #pragma unroll
@@ -159,7 +240,34 @@ ct_corr2d(const __grid_constant__ CtParams p)
     const int gx = gx0 + lx;
     const int gy = gy0 + ly;
 
-#if CT_SMEM
+#if CT_SMEM && CT_TMA
+    extern __shared__ float4 ct_smem4[];
+    __shared__ unsigned long long ct_bar;
+    unsigned char* const raw = reinterpret_cast<unsigned char*>(ct_smem4);
+    const unsigned mis = ct_sa(raw) & 127u;   // the tensor copy lands on a 128-byte boundary
+    ct_in_t* const sm = reinterpret_cast<ct_in_t*>(raw + (mis ? 128u - mis : 0u));
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(ct_sa(&ct_bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(ct_sa(&ct_bar)),
+                     "r"((unsigned)(CT_HALO_H * CT_SWT * CT_ESZ + CT_TEST_EXTRA_TX))
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+            "[%4];\n" ::"r"(ct_sa(sm)),
+            "l"(&p.tmap), "r"(gx0), "r"(gy0), "r"(ct_sa(&ct_bar))
+            : "memory");
+    }
+    __syncthreads();   // the barrier is initialised before anyone waits on it
+    if (!ct_bar_wait(&ct_bar, 0u)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            atomicOr(p.err, 1u);
+            (void)ct_bar_wait(&ct_bar, 0u);
+        }
+        return;
+    }
+#define CT_LOAD_ROW(w, r) ct_row_staged(w, sm + (ly + (r)) * CT_SWT + lx)
+#elif CT_SMEM
     extern __shared__ float4 ct_smem4[];
     float* sm = reinterpret_cast<float*>(ct_smem4);
     {

@@ -113,6 +113,26 @@ struct Variant {
 };
 using VariantPtr = std::shared_ptr<Variant>;
 
+// Writes the 128-byte tensor map (64-byte aligned `map`) of an image of
+// in_w x in_h elements, rows in_pitch elements apart, 16-byte aligned, whose
+// box (box_w x box_h elements, each at most 256, box_w a multiple of 16 bytes)
+// is the halo of one tile; elements outside the image read as zero.
+ct_status encode_halo_map(void* map, const void* d_image, int dtype, int64_t in_w, int64_t in_h, int64_t in_pitch,
+                          int64_t box_w, int64_t box_h);
+constexpr size_t kTensorMapBytes = 128;
+
+// The single-problem kernel stages its halo with one tensor copy when it uses
+// shared memory and the halo box fits (at most 256 x 256 elements).
+int64_t halo_box_w(const ct_config& c, int fw, int dtype);
+int64_t halo_box_h(const ct_config& c, int fh);
+bool tma_staged(const ct_config& c, int fw, int fh, int dtype);
+// Device word whose bit 0 the kernels set when a bounded wait gave up
+// (allocated on first use on each device; NULL without a device).
+unsigned* device_error_word();
+// Reads the current device's error word (synchronously) and clears it;
+// true when bit 0 was set.
+bool take_device_error();
+
 // Compiles with NVRTC, consulting the on-disk cache (thread safe; no device needed).
 VariantPtr compile_variant(const VariantKey& k, const std::string& cache_dir);
 VariantPtr compile_source(const char* src, size_t len, const char* prog_name, const std::vector<std::string>& opts,

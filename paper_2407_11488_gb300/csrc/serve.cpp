@@ -358,8 +358,8 @@ bool ct_server::launch_locked(Launch& L)
         d.pad = 0;
         const TileCfg& c = buckets[(size_t)r.bucket].cfg;
         const ct_status ms = encode_halo_map(maps + i * kTensorMapBytes, r.d_image, o.dtype, d.in_w, d.in_h,
-                                             r.in_pitch, halo_box_w(threads, c, r.rq.filter_w, o.dtype),
-                                             halo_box_h(threads, c, r.rq.filter_h));
+                                             r.in_pitch, batch_box_w(threads, c, r.rq.filter_w, o.dtype),
+                                             batch_box_h(threads, c, r.rq.filter_h));
         if (ms != CT_OK) {
             fatal = ms;
             fatal_msg = last_error();

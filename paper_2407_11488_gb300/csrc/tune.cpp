@@ -292,6 +292,7 @@ private:
             abort = true;
             return CT_ERR_CUDA;
         }
+        if (take_device_error()) return CT_ERR_TIMEOUT;   // a launch gave up waiting for its input copy
         summarize(t, m);
         return CT_OK;
     }

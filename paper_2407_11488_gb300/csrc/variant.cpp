@@ -1,5 +1,7 @@
 // Variant builder: NVRTC compile of the correlation template to an sm_103a
 // cubin, on-disk and in-memory caches, module loading and the launch.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include "ct_internal.hpp"
 
 #include <nvrtc.h>
@@ -76,9 +78,86 @@ static std::vector<std::string> nvrtc_options(const VariantKey& k)
     def("CT_FW", k.fw);
     def("CT_FH", k.fh);
     def("CT_DTYPE", k.dtype);
+    def("CT_TMA", tma_staged(k.cfg, k.fw, k.fh, k.dtype) ? 1 : 0);
     add_env_options(o);
     return o;
 }
+
+int64_t halo_box_w(const ct_config& c, int fw, int dtype)
+{
+    return round_up((int64_t)c.block_x * c.tile_x + fw - 1, 16 / elem_size(dtype));
+}
+int64_t halo_box_h(const ct_config& c, int fh) { return (int64_t)c.block_y * c.tile_y + fh - 1; }
+bool tma_staged(const ct_config& c, int fw, int fh, int dtype)
+{
+    return c.use_smem && halo_box_w(c, fw, dtype) <= 256 && halo_box_h(c, fh) <= 256 &&
+           ((int64_t)c.block_x * c.tile_x * elem_size(dtype)) % 16 == 0;
+}
+
+unsigned* device_error_word()
+{
+    static std::mutex mu;
+    static unsigned* words[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> g(mu);
+    if (!words[dev]) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, 256) != cudaSuccess || cudaMemset(p, 0, 256) != cudaSuccess) {
+            cudaGetLastError();
+            if (p) cudaFree(p);
+            return nullptr;
+        }
+        words[dev] = static_cast<unsigned*>(p);
+    }
+    return words[dev];
+}
+
+bool take_device_error()
+{
+    unsigned* w = device_error_word();
+    if (!w) return false;
+    unsigned v = 0;
+    if (cudaMemcpy(&v, w, 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (v & 1u) cudaMemset(w, 0, 4);
+    return (v & 1u) != 0;
+}
+
+ct_status encode_halo_map(void* map, const void* d_image, int dtype, int64_t in_w, int64_t in_h, int64_t in_pitch,
+                          int64_t box_w, int64_t box_h)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode) return fail(CT_ERR_CUDA, "the driver offers no cuTensorMapEncodeTiled");
+    const cuuint64_t dims[2] = {(cuuint64_t)in_w, (cuuint64_t)in_h};
+    const cuuint64_t strides[1] = {(cuuint64_t)(in_pitch * elem_size(dtype))};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r =
+        encode(static_cast<CUtensorMap*>(map),
+               dtype == CT_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+               const_cast<void*>(d_image), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(CT_ERR_INVALID_ARG, "cuTensorMapEncodeTiled failed (%d) for a %lldx%lld image, box %lldx%lld",
+                    (int)r, (long long)in_w, (long long)in_h, (long long)box_w, (long long)box_h);
+    return CT_OK;
+}
+
 
 static uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull)
 {
@@ -219,7 +298,10 @@ VariantPtr compile_variant(const VariantKey& k, const std::string& cache_dir)
     ct_problem p{};
     p.filter_w = k.fw;
     p.filter_h = k.fh;
-    v->smem = smem_bytes(p, k.cfg);
+    // a tensor-staged halo lands on a 128-byte boundary: 128 bytes of slack
+    v->smem = tma_staged(k.cfg, k.fw, k.fh, k.dtype)
+                  ? halo_box_w(k.cfg, k.fw, k.dtype) * halo_box_h(k.cfg, k.fh) * elem_size(k.dtype) + 128
+                  : smem_bytes(p, k.cfg);
     if (v->status != CT_OK) v->error = "NVRTC failed for " + k.describe() + ": " + v->error;
     return v;
 }
@@ -363,10 +445,13 @@ ct_status check_buffers(const ct_problem& p, const void* d_image, const void* h_
     return CT_OK;
 }
 
-// Parameter block of ct_corr2d, laid out as the device struct CtParams:
-// in, out, in_pitch, out_pitch (8 bytes each), out_w, out_h, in_w, in_h
-// (4 bytes each), then filter_h*filter_w floats.
-static constexpr size_t kParamHeader = 48;
+// Parameter block of ct_corr2d, laid out as the device struct CtParams: the
+// image's tensor map (128 bytes, 64-byte aligned; zero for variants that do
+// not use it), in, out, in_pitch, out_pitch (8 bytes each), out_w, out_h,
+// in_w, in_h (4 bytes each), the error word's address (8 bytes), then
+// filter_h*filter_w floats; the struct's size is a multiple of 64 bytes.
+static constexpr size_t kParamHeader = 184;
+static constexpr size_t kParamMax = (kParamHeader + 4 * CT_MAX_FILTER * CT_MAX_FILTER + 63) / 64 * 64;
 
 ct_status launch_variant(Variant& v, const ct_problem& p, const void* d_image, const void* h_filter,
                          float* d_out, cudaStream_t stream)
@@ -381,16 +466,25 @@ ct_status launch_variant(Variant& v, const ct_problem& p, const void* d_image, c
         return fail(CT_ERR_INVALID_ARG, "grid %lldx%lld exceeds the launch limits for this config", (long long)gx,
                     (long long)gy);
     const int nt = p.filter_w * p.filter_h;
-    alignas(16) unsigned char buf[kParamHeader + 4 * CT_MAX_FILTER * CT_MAX_FILTER];
+    alignas(64) unsigned char buf[kParamMax];
+    memset(buf, 0, kTensorMapBytes);
+    if (tma_staged(c, p.filter_w, p.filter_h, p.dtype)) {
+        s = encode_halo_map(buf, d_image, p.dtype, in_w(p), in_h(p), p.in_pitch, halo_box_w(c, p.filter_w, p.dtype),
+                            halo_box_h(c, p.filter_h));
+        if (s != CT_OK) return s;
+    }
+    unsigned* err = device_error_word();
+    if (!err) return fail(CT_ERR_CUDA, "no device error word");
     const void* in_ptr = d_image;
     void* out_ptr = d_out;
     const int64_t ipitch = p.in_pitch, opitch = p.out_pitch;
     const int32_t dims[4] = {p.out_w, p.out_h, (int32_t)in_w(p), (int32_t)in_h(p)};
-    memcpy(buf + 0, &in_ptr, 8);
-    memcpy(buf + 8, &out_ptr, 8);
-    memcpy(buf + 16, &ipitch, 8);
-    memcpy(buf + 24, &opitch, 8);
-    memcpy(buf + 32, dims, 16);
+    memcpy(buf + 128, &in_ptr, 8);
+    memcpy(buf + 136, &out_ptr, 8);
+    memcpy(buf + 144, &ipitch, 8);
+    memcpy(buf + 152, &opitch, 8);
+    memcpy(buf + 160, dims, 16);
+    memcpy(buf + 176, &err, 8);
     float* taps = reinterpret_cast<float*>(buf + kParamHeader);
     if (p.dtype == CT_F32) {
         memcpy(taps, h_filter, 4 * (size_t)nt);

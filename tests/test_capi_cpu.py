@@ -107,15 +107,19 @@ def test_space_from_json(ctlib):
 
 
 def test_nvrtc_compiles_variants_without_gpu(ctlib):
-    """NVRTC builds sm_103a cubins on a machine with no GPU."""
+    """NVRTC builds sm_103a cubins on a machine with no GPU.  A variant's
+    dynamic shared memory is its halo tile; variants whose halo box (width
+    rounded to 16 bytes) is at most 256 x 256 elements load it with one tensor
+    copy and ask for 128 bytes more, to place it on a 128-byte boundary."""
     p = ctlib.make_problem(4096, 4096, 17, 17)
-    for c in [ctlib.default_config(), ctlib.config(32, 4, 4, 8, 1, 1), ctlib.config(16, 8, 3, 5, 1, 0),
-              ctlib.config(64, 2, 2, 2, 0, 1)]:
+    for c, tensor_copy in [(ctlib.default_config(), False), (ctlib.config(32, 4, 4, 8, 1, 1), True),
+                           (ctlib.config(16, 8, 3, 5, 1, 0), True), (ctlib.config(64, 2, 2, 2, 0, 1), False),
+                           (ctlib.config(128, 2, 2, 4, 1, 1), False), (ctlib.config(16, 16, 4, 2, 1, 1), True)]:
         info = ctlib.compile_variant(p, c)
         assert info["cubin_bytes"] > 1000 and info["regs"] > 0, (c, info)
         assert info["smem_bytes"] == ospace.smem_bytes(
             {"block_x": c.block_x, "block_y": c.block_y, "tile_x": c.tile_x, "tile_y": c.tile_y,
-             "smem": c.use_smem}, 17, 17)
+             "smem": c.use_smem}, 17, 17) + (128 if tensor_copy else 0), c
     pb = ctlib.make_problem(1024, 1024, 9, 9, dtype=ctlib.CT_BF16)
     assert ctlib.compile_variant(pb, ctlib.config(32, 4, 4, 4, 1, 1))["regs"] > 0
 

@@ -3,6 +3,7 @@ the C-ABI.  Bar: |gpu - oracle| <= 1e-5 * sum|in*f| per pixel (FP32);
 bit-exact where the arithmetic is exact (integer inputs, impulse filters).
 Every launch also checks sentinel guard bands around the output."""
 import concurrent.futures as cf
+import time
 
 import numpy as np
 import pytest
@@ -11,7 +12,7 @@ import torch
 import oracle
 import synthetic
 from oracle import space as ospace
-from tests.gpu_util import assert_parity, run_config, upload_image
+from tests.gpu_util import SENTINEL, assert_parity, run_config, upload_image
 
 pytestmark = pytest.mark.gpu
 
@@ -322,3 +323,57 @@ def test_host_entry_point_async_overlapping_calls(ctlib, cuda_device):
         d = upload_image(probs[k][0], cuda_device)
         ref, ok = run_config(ctlib, d, probs[k][1], c, ow, oh, in_w=ow + fw - 1)
         assert np.array_equal(h_outs[k].numpy()[:, :ow].view(np.uint32), ref.view(np.uint32))
+
+
+def test_tensor_copy_variants_leave_the_error_word_clear(ctlib, cuda_device):
+    """Variants staged by a tensor copy (halo box <= 256 x 256) and by
+    per-thread copies agree bit for bit on an image whose row padding holds
+    NaN (the tensor copy reads zeros past the row, the per-thread copy the
+    padding; neither reaches a stored output), and no wait gives up."""
+    ow, oh, fs = 700, 333, 17
+    img, f = synthetic.make_problem(11, ow, oh, fs, fs, pitch_align=8, pad_value=np.nan)
+    d_img = upload_image(img, cuda_device)
+    ref, S = oracle.corr2d_f64(img, f, ow, oh)
+    ctlib.device_check()
+    outs = []
+    for c in [ctlib.config(16, 16, 4, 2, 1, 1), ctlib.config(32, 4, 4, 8, 1, 0), ctlib.config(128, 2, 2, 4, 1, 1),
+              ctlib.config(32, 8, 1, 1, 0, 0)]:
+        out, ok = run_config(ctlib, d_img, f, c, ow, oh, in_w=ow + fs - 1)
+        assert ok
+        assert_parity(out, ref, S, repr(c))
+        outs.append(out)
+    for o in outs[1:]:
+        assert np.array_equal(o.view(np.uint32), outs[0].view(np.uint32))
+    ctlib.device_check()
+
+
+def test_tensor_copy_wait_timeout_is_reported(ctlib, cuda_device, monkeypatch):
+    """A tensor-staged variant compiled to expect 16 bytes more than its copy
+    delivers cannot complete its wait: every block gives up after the bounded
+    wait and stores nothing, ct_device_check reports CT_ERR_TIMEOUT, and the
+    context stays usable."""
+    ow = oh = 128
+    img, f = synthetic.make_problem(5, ow, oh, 5, 5)
+    d_img = upload_image(img, cuda_device)
+    c = ctlib.config(32, 4, 4, 2, 1, 1)          # halo box 132 x 12: staged by a tensor copy
+    ctlib.device_check()
+    ctlib.clear_cache()                           # in-memory variants are keyed by configuration only
+    monkeypatch.setenv("CONVTUNE_NVRTC_EXTRA", "-DCT_TEST_EXTRA_TX=16")
+    try:
+        t0 = time.time()
+        out, ok = run_config(ctlib, d_img, f, c, ow, oh, in_w=ow + 4)
+        assert time.time() - t0 < 30.0
+    finally:
+        monkeypatch.delenv("CONVTUNE_NVRTC_EXTRA")
+        ctlib.clear_cache()
+    assert ok
+    assert np.all(out.view(np.uint32) == np.array(SENTINEL).view(np.uint32))   # nothing stored
+    with pytest.raises(ctlib.CTError) as e:
+        ctlib.device_check()
+    assert e.value.status == -7
+    ctlib.device_check()                          # cleared
+    ref, S = oracle.corr2d_f64(img, f, ow, oh)
+    out, ok = run_config(ctlib, d_img, f, c, ow, oh, in_w=ow + 4)
+    assert ok
+    assert_parity(out, ref, S, "after a timed-out launch")
+    ctlib.device_check()
