@@ -324,10 +324,22 @@ def run_ours(args):
         n_valid = tab.info["n_valid_space"]
         a = tab.analysis
         analysis = {"tuned_vs_median": a["tuned_vs_median"], "frac_within_10pct": a["frac_within_10pct"],
-                    "impact": a["impact"],
+                    "impact": a["impact"], "local_minima": a["n_minima"],
                     "proportion_of_centrality": {f"{p:.2f}": v for p, v in a["cp"].items()},
                     "perf_quantiles_gflops": a["quantiles"],
                     "analysis_over": f"{a['n_valid']} configs measured by {args.strategy}"}
+        ranked = sorted(tab.valid(), key=lambda r: (r["t_med_ms"], r["index"]))
+        cfg_key = ("block_x", "block_y", "tile_x", "tile_y", "use_smem", "unroll")
+
+        def _short(r):
+            return {"config": [r[k] for k in cfg_key], "ms": r["t_med_ms"], "gflops": r["gflops"],
+                    "regs": r["regs"], "smem_bytes": r["smem_bytes"]}
+        analysis["top10"] = [_short(r) for r in ranked[:10]]
+        best_mode = {}
+        for r in ranked:
+            best_mode.setdefault(f"smem{r['use_smem']}_unroll{r['unroll']}", _short(r))
+        analysis["best_per_staging_unroll"] = best_mode
+        analysis["n_spilling"] = sum(1 for r in tab.valid() if r["spill_bytes"] > 0)
 
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(int(2 * max(info.l2_bytes, 64 << 20)), dtype=torch.uint8, device=dev)
