@@ -20,13 +20,12 @@
 //                     (through L1);
 //                  1: the block stages its input tile plus halo in shared
 //                     memory, then reads windows from there
-//   CT_TMA         (chosen by the host for CT_SMEM = 1 when the halo box is
-//                  at most 256 x 256 elements) 1: one thread stages the halo
-//                  with a 2D tensor copy (the tensor map in the parameter
-//                  block; elements outside the image arrive as zeros) that
-//                  completes on an mbarrier; BF16 stays BF16 in shared memory
-//                  and is widened when a row enters registers.  0: every
-//                  thread copies 16-byte chunks
+//   CT_TMA         (chosen by the host for FP32 images with CT_SMEM = 1 when
+//                  the halo box is at most 256 x 256 elements) 1: one thread
+//                  stages the halo with a 2D tensor copy (the tensor map in
+//                  the parameter block; elements outside the image arrive as
+//                  zeros) that completes on an mbarrier.  0: every thread
+//                  copies 16-byte chunks (BF16 widened to FP32 on the way)
 //   CT_UNROLL      1: fully unrolled; input rows slide through a register
 //                     window and each row feeds every output row that uses it;
 //                  0: the loop over filter rows stays rolled
@@ -46,6 +45,9 @@
 #endif
 #ifndef CT_TMA
 #define CT_TMA 0
+#endif
+#if CT_TMA && CT_DTYPE != 0
+#error "tensor-copy staging is for FP32 images"
 #endif
 // Test hook: bytes expected on top of those the tensor copy delivers; a
 // nonzero value makes the wait run out.  0 in every normal build.
@@ -182,13 +184,12 @@ __device__ __forceinline__ bool ct_bar_wait(unsigned long long* bar, unsigned pa
     }
 }
 
-// One input row of the thread's window from the tensor-copied halo (storage
-// dtype, CT_SWT elements per row), widened to FP32.
-__device__ __forceinline__ void ct_row_staged(float (&w)[CT_WWV], const ct_in_t* __restrict__ s)
+// One input row of the thread's window from the tensor-copied halo (CT_SWT
+// floats per row).
+__device__ __forceinline__ void ct_row_staged(float (&w)[CT_WWV], const float* __restrict__ s)
 {
 #pragma unroll
     for (int k = 0; k < CT_WWV; k += CT_VW) {
-#if CT_DTYPE == 0
         if (CT_VW == 4) {
             const float4 v = *reinterpret_cast<const float4*>(s + k);
             w[k] = v.x; w[k + 1] = v.y; w[k + 2] = v.z; w[k + 3] = v.w;
@@ -198,18 +199,6 @@ __device__ __forceinline__ void ct_row_staged(float (&w)[CT_WWV], const ct_in_t*
         } else {
             w[k] = s[k];
         }
-#else
-        if (CT_VW == 4) {
-            const uint2 v = *reinterpret_cast<const uint2*>(s + k);
-            w[k] = __uint_as_float(v.x << 16); w[k + 1] = __uint_as_float(v.x & 0xffff0000u);
-            w[k + 2] = __uint_as_float(v.y << 16); w[k + 3] = __uint_as_float(v.y & 0xffff0000u);
-        } else if (CT_VW == 2) {
-            const ct_u32 v = *reinterpret_cast<const ct_u32*>(s + k);
-            w[k] = __uint_as_float(v << 16); w[k + 1] = __uint_as_float(v & 0xffff0000u);
-        } else {
-            w[k] = ct_bf16(s[k]);
-        }
-#endif
     }
 }
 #endif
@@ -245,7 +234,7 @@ ct_corr2d(const __grid_constant__ CtParams p)
     __shared__ unsigned long long ct_bar;
     unsigned char* const raw = reinterpret_cast<unsigned char*>(ct_smem4);
     const unsigned mis = ct_sa(raw) & 127u;   // the tensor copy lands on a 128-byte boundary
-    ct_in_t* const sm = reinterpret_cast<ct_in_t*>(raw + (mis ? 128u - mis : 0u));
+    float* const sm = reinterpret_cast<float*>(raw + (mis ? 128u - mis : 0u));
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(ct_sa(&ct_bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");

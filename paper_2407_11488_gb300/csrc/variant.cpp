@@ -88,9 +88,12 @@ int64_t halo_box_w(const ct_config& c, int fw, int dtype)
     return round_up((int64_t)c.block_x * c.tile_x + fw - 1, 16 / elem_size(dtype));
 }
 int64_t halo_box_h(const ct_config& c, int fh) { return (int64_t)c.block_y * c.tile_y + fh - 1; }
+// FP32 only: a BF16 halo copied as is would be widened at every window load
+// (each element is loaded by up to TY + FH - 1 rows of windows), while the
+// per-thread staging widens each element once.
 bool tma_staged(const ct_config& c, int fw, int fh, int dtype)
 {
-    return c.use_smem && halo_box_w(c, fw, dtype) <= 256 && halo_box_h(c, fh) <= 256 &&
+    return dtype == CT_F32 && c.use_smem && halo_box_w(c, fw, dtype) <= 256 && halo_box_h(c, fh) <= 256 &&
            ((int64_t)c.block_x * c.tile_x * elem_size(dtype)) % 16 == 0;
 }
 
