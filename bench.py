@@ -66,6 +66,8 @@ def parse():
                     help="skip: time only the batched path (profiling)")
     ap.add_argument("--batch-plain-evals", type=int, default=120,
                     help="annealing budget per filter size for the per-problem path of the batch workload")
+    ap.add_argument("--batch-solo-waves", type=int, default=0,
+                    help="batch: problems filling this many GPU waves run as their own launch (0: library default)")
     ap.add_argument("--strategy", choices=["random", "anneal", "brute"], default="anneal")
     ap.add_argument("--extra-strategies", default="", help="comma list also run (wall time reported)")
     ap.add_argument("--seed", type=int, default=0, help="strategy seed")
@@ -487,8 +489,12 @@ def run_ours(args):
 
 def run_batch(args):
     """64 uneven correlations: the plain per-problem path (one ct_conv2d per
-    problem with the configuration tuned for its filter size) against one
-    persistent launch of the batched kernel (graph), same inputs and outputs."""
+    problem with the configuration tuned for its filter size; also timed as
+    one captured CUDA graph, which leaves out the host's per-launch cost)
+    against one graph launch of the batch plan (problems that fill the GPU
+    alone as their own launches, the rest in one persistent launch; also
+    timed with every problem in the persistent launch), same inputs and
+    outputs."""
     import numpy as np
     import torch
 
@@ -549,9 +555,12 @@ def run_batch(args):
 
     t0 = time.time()
     batch = ct.Batch([(d_img, f, out, side + fs - 1) for (_, f, d_img, out, side, fs) in probs], tune=True,
-                     max_tune_items=6)
+                     max_tune_items=6, solo_waves=args.batch_solo_waves)
     batch_plan_s = time.time() - t0
     binfo = batch.info()
+    # the same plan with every problem in the persistent launch (no solo launches)
+    persistent = ct.Batch([(d_img, f, out, side + fs - 1) for (_, f, d_img, out, side, fs) in probs], tune=True,
+                          max_tune_items=6, solo_waves=-1) if binfo["n_solo"] else batch
 
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(int(2 * max(info.l2_bytes, 64 << 20)), dtype=torch.uint8, device=dev)
@@ -590,6 +599,16 @@ def run_batch(args):
     ms_batch = timed(batch_step, k, max(3, args.warmup), "batch_timed")
     tb1 = time.time()
     ms_plain = timed(plain_step, k, max(3, args.warmup), "plain_timed") if plain_args else [float("nan")]
+    ms_persist = timed(lambda: persistent.run(stream), k, max(3, args.warmup), "persistent_timed")
+    # the per-problem launches captured in one CUDA graph: their GPU time without the host's launch cost
+    ms_plain_graph = [float("nan")]
+    if plain_args:
+        g_plain = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            stream.synchronize()
+            with torch.cuda.graph(g_plain, stream=stream):
+                plain_step()
+        ms_plain_graph = timed(lambda: g_plain.replay(), k, max(3, args.warmup), "plain_graph_timed")
     clocks.stop()
     # the batched outputs equal the per-problem outputs bit for bit
     batch_step()
@@ -632,6 +651,10 @@ def run_batch(args):
         "batched_p50_ms": statistics.median(ms_batch), "batched_p99_ms": p99,
         "plain_gflops": world * flops / (t_p * 1e-3) / 1e9, "plain_ms_per_step": t_p,
         "batched_vs_plain": t_p / t_b, "bit_identical_to_plain": identical,
+        "plain_graph_ms_per_step": statistics.mean(ms_plain_graph),
+        "batched_vs_plain_graph": statistics.mean(ms_plain_graph) / t_b,
+        "persistent_only_ms_per_step": statistics.mean(ms_persist),
+        "persistent_only_vs_plain": t_p / statistics.mean(ms_persist),
         "composite_bound_ms": peak_s * 1e3, "batched_frac_of_bound": peak_s * 1e3 / t_b,
         "batch": {"buckets": batch.buckets(), **binfo, "plan_s": batch_plan_s},
         "plain_tuning": {"wall_s": plain_tune_s, **tuning},

@@ -337,6 +337,13 @@ CT_API ct_status ct_table_analyze(const ct_table* t, const ct_space* s, double f
  * Eq. 3), the alternative the bucket's summed time.  Results are bit-identical
  * to ct_conv2d on each problem.
  *
+ * Problems big enough to fill the GPU on their own (opts->solo_waves) run
+ * instead as their own launch of the single-problem kernel, whose taps are
+ * constant-bank operands; its configuration is tuned per filter size at
+ * create (annealing, opts->solo_evals evaluations, on the largest such
+ * problem, whose buffers the tuner uses).  The plan's graph holds these
+ * launches first, then the persistent launch of the other problems.
+ *
  * Each item's input halo and filter taps reach shared memory by tensor-memory
  * copies (one 2D tensor map per problem, encoded at create for the bucket's
  * tile); a tile's halo box is at most 256 x 256 elements, and a problem spans
@@ -366,15 +373,21 @@ typedef struct {
     int32_t side_split;     /* image side splitting a filter size into two buckets (0: 512; < 0: no split) */
     int32_t blocks_per_sm;  /* resident blocks per SM of the persistent grid (0: occupancy query) */
     int32_t max_tune_items; /* problems per bucket measured while tuning (0: 12) */
+    int32_t solo_waves;     /* a problem whose tiles under its solo configuration fill at least this many
+                               waves of the GPU runs as its own ct_corr2d launch in the plan's graph
+                               (0: 1; < 0: every problem goes to the persistent launch) */
+    int32_t solo_evals;     /* annealing budget per filter size for the solo configuration (0: 60) */
     int32_t reserved;
 } ct_batch_opts;
 
 typedef struct {
     int32_t n_items, n_buckets;
-    int64_t n_work;         /* work items (tiles) per run */
+    int64_t n_work;         /* work items (tiles) of the persistent launch per run */
     int32_t grid, threads;
     int32_t smem_bytes, regs;
     double plan_ms, tune_ms, compile_cpu_ms;
+    int32_t n_solo;         /* problems run as their own launch */
+    int32_t reserved;
 } ct_batch_info;
 
 typedef struct ct_batch ct_batch;
@@ -400,7 +413,8 @@ CT_API ct_status ct_batch_info_get(const ct_batch* b, ct_batch_info* out);
  * (NaN when the bucket was not tuned). */
 CT_API ct_status ct_batch_bucket(const ct_batch* b, int32_t k, int32_t* filter_w, int32_t* filter_h,
                                  int32_t* n_items, ct_bucket_config* cfg, double* pp);
-/* Bucket index of item i (in the order given to ct_batch_create). */
+/* Bucket index of item i (in the order given to ct_batch_create); -1 for a
+ * problem that runs as its own launch. */
 CT_API int32_t ct_batch_item_bucket(const ct_batch* b, int32_t i);
 CT_API void ct_batch_free(ct_batch* b);
 

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <map>
 #include <numeric>
 
 namespace ct {
@@ -107,6 +108,9 @@ struct ct_batch {
     std::vector<int> filt_off;
     std::vector<Bucket> buckets;
     VariantPtr module;
+    // problems run as their own single-problem launch, with their variant
+    std::vector<int> solo_items;
+    std::vector<VariantPtr> solo_vars;
     void* d_probs = nullptr;
     void* d_work = nullptr;
     float* d_filters = nullptr;
@@ -359,6 +363,84 @@ ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o,
     return CT_OK;
 }
 
+// Problems that fill at least `waves` waves of the GPU on their own go solo.
+// For every filter size whose largest problem could (one output per resident
+// thread and wave), the single-problem configuration is tuned on that
+// problem (annealing, o.solo_evals evaluations, on its own buffers); each
+// problem of that size whose tile count under the configuration reaches
+// waves x SMs x resident blocks then runs as its own launch of it.
+ct_status plan_solo(ct_batch& B, const ct_batch_opts& o, std::vector<char>& solo, double* tune_ms)
+{
+    const int waves = o.solo_waves == 0 ? 1 : o.solo_waves;
+    if (waves <= 0) return CT_OK;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int n = (int)B.items.size();
+    auto area = [&](int i) { return (int64_t)B.items[(size_t)i].out_w * B.items[(size_t)i].out_h; };
+    std::map<std::pair<int, int>, int> largest;
+    for (int i = 0; i < n; ++i) {
+        if (area(i) < (int64_t)waves * sms * 2048) continue;
+        const auto key = std::make_pair(B.items[(size_t)i].filter_w, B.items[(size_t)i].filter_h);
+        auto f = largest.find(key);
+        if (f == largest.end() || area(i) > area(f->second)) largest[key] = i;
+    }
+    if (largest.empty()) return CT_OK;
+    const double t0 = now_ms();
+    ct_space* sp = nullptr;
+    ct_status st = ct_space_builtin("full", &sp);
+    if (st != CT_OK) return st;
+    struct SpaceGuard {
+        ct_space* s;
+        ~SpaceGuard() { ct_space_free(s); }
+    } sg{sp};
+    std::vector<std::pair<int64_t, int>> picked;   // (area, item)
+    std::map<int, VariantPtr> var_of;
+    for (const auto& kv : largest) {
+        const ct_batch_item& big = B.items[(size_t)kv.second];
+        const ct_problem p{big.out_w, big.out_h, big.filter_w, big.filter_h, big.in_pitch, big.out_pitch, B.dtype, 0};
+        ct_tune_opts to{};
+        to.seed = 1;
+        to.max_evals = o.solo_evals > 0 ? o.solo_evals : 60;
+        to.anneal_chains = 4;
+        ct_config best{};
+        ct_table* t = nullptr;
+        st = ct_tune(&p, sp, CT_ANNEAL, &to, big.d_image, big.h_filter, big.d_out, &best, &t);
+        if (t) ct_table_free(t);
+        if (st != CT_OK)
+            return fail(st, "tuning the single-problem configuration for filter %dx%d: %s", big.filter_w,
+                        big.filter_h, last_error());
+        VariantPtr v = compile_variant(VariantKey{best, big.filter_w, big.filter_h, B.dtype}, cache_dir_setting());
+        if (!v || v->status != CT_OK)
+            return fail(CT_ERR_COMPILE, "single-problem variant: %s", v ? v->error.c_str() : "no variant");
+        if ((st = load_variant(*v)) != CT_OK) return st;
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)v->kern, best.block_x * best.block_y,
+                                                          (size_t)v->smem) != cudaSuccess ||
+            nb <= 0) {
+            cudaGetLastError();
+            nb = 1;
+        }
+        const int64_t slots = (int64_t)waves * sms * nb;
+        const int64_t tw = (int64_t)best.block_x * best.tile_x, th = (int64_t)best.block_y * best.tile_y;
+        for (int i = 0; i < n; ++i) {
+            const ct_batch_item& it = B.items[(size_t)i];
+            if (it.filter_w != big.filter_w || it.filter_h != big.filter_h) continue;
+            if (((it.out_w + tw - 1) / tw) * ((it.out_h + th - 1) / th) < slots) continue;
+            solo[(size_t)i] = 1;
+            picked.emplace_back(area(i), i);
+            var_of[i] = v;
+        }
+    }
+    std::stable_sort(picked.begin(), picked.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    for (const auto& pi : picked) {
+        B.solo_items.push_back(pi.second);
+        B.solo_vars.push_back(var_of[pi.second]);
+    }
+    *tune_ms = now_ms() - t0;
+    return CT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -409,12 +491,19 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
                 arena.push_back(v);
             }
     }
-    // buckets: filter size, then image side class
+    // problems that fill the GPU alone run as their own launch of the
+    // single-problem kernel (constant-bank taps), configuration tuned per
+    // filter size on its largest problem
     B->item_bucket.assign((size_t)n, -1);
+    std::vector<char> solo((size_t)n, 0);
+    double solo_tune_ms = 0.0;
+    if ((st = plan_solo(*B, o, solo, &solo_tune_ms)) != CT_OK) return st;
+    // buckets: filter size, then image side class
     for (int pass = 0; pass < 2; ++pass) {
         B->buckets.clear();
         for (int i = 0; i < n; ++i) {
             const ct_batch_item& it = items[i];
+            if (solo[(size_t)i]) continue;
             const int side = (pass == 0 && split > 0 && std::max(it.out_w, it.out_h) >= split) ? 1 : 0;
             int k = -1;
             for (size_t b = 0; b < B->buckets.size(); ++b)
@@ -466,69 +555,90 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
             }
         }
     }
-    B->info.tune_ms = o.tune ? now_ms() - tt0 : 0.0;
-    // the persistent kernel with every bucket's tile routine
-    std::vector<BucketDesc> desc;
-    for (const auto& bk : B->buckets) desc.push_back({bk.fw, bk.fh, bk.cfg});
-    B->module = compile_batch(threads, o.dtype, desc, cache_dir_setting());
-    compile_cpu += B->module->compile_ms;
-    if (B->module->status != CT_OK) return fail(CT_ERR_COMPILE, "%s", B->module->error.c_str());
-    if (B->module->smem > smem_limit) return fail(CT_ERR_INVALID_CONFIG, "batch kernel needs too much shared memory");
-    if ((st = load_variant(*B->module)) != CT_OK) return st;   // also fills in the register count
-    // problem table, tensor maps and work list: most expensive tiles first
+    B->info.tune_ms = (o.tune ? now_ms() - tt0 : 0.0) + solo_tune_ms;
+    const bool persistent = !B->buckets.empty();
     std::vector<DevProblem> probs;
-    std::vector<unsigned char> maps((size_t)n * kTensorMapBytes);
-    for (int i = 0; i < n; ++i) {
-        const int b = B->item_bucket[(size_t)i];
-        probs.push_back(dev_problem(*B, i, b, B->buckets[(size_t)b].cfg));
-        alignas(64) unsigned char map[kTensorMapBytes];
-        if ((st = item_map(*B, i, B->buckets[(size_t)b].cfg, map)) != CT_OK) return st;
-        memcpy(maps.data() + (size_t)i * kTensorMapBytes, map, kTensorMapBytes);
-    }
-    std::vector<int> border(B->buckets.size());
-    std::iota(border.begin(), border.end(), 0);
-    auto tile_cost = [&](int b) {
-        const auto& k = B->buckets[(size_t)b];
-        return (double)k.fw * k.fh * tile_w(threads, k.cfg) * tile_h(threads, k.cfg);
-    };
-    std::stable_sort(border.begin(), border.end(), [&](int a, int b) { return tile_cost(a) > tile_cost(b); });
+    std::vector<unsigned char> maps((size_t)n * kTensorMapBytes, 0);
     std::vector<WorkItem> work;
-    for (int b : border) {
-        std::vector<int> its = B->buckets[(size_t)b].items;
-        std::stable_sort(its.begin(), its.end(), [&](int a, int c) {
-            return (int64_t)items[a].out_w * items[a].out_h > (int64_t)items[c].out_w * items[c].out_h;
-        });
-        for (int i : its) {
-            const TileCfg& c = B->buckets[(size_t)b].cfg;
-            if (!tile_grid_ok(items[i].out_w, items[i].out_h, tile_w(threads, c), tile_h(threads, c)))
-                return fail(CT_ERR_UNSUPPORTED, "batch item %d: more than %lld tiles along one side", i,
-                            (long long)kMaxTilesPerSide);
-            int64_t tx = 0;
-            const int64_t nt = tiles_of(items[i], threads, c, &tx);
-            for (int64_t k = 0; k < nt; ++k) work.push_back(work_item((uint32_t)i, k, tx));
+    if (persistent) {
+        // the persistent kernel with every bucket's tile routine
+        std::vector<BucketDesc> desc;
+        for (const auto& bk : B->buckets) desc.push_back({bk.fw, bk.fh, bk.cfg});
+        B->module = compile_batch(threads, o.dtype, desc, cache_dir_setting());
+        compile_cpu += B->module->compile_ms;
+        if (B->module->status != CT_OK) return fail(CT_ERR_COMPILE, "%s", B->module->error.c_str());
+        if (B->module->smem > smem_limit)
+            return fail(CT_ERR_INVALID_CONFIG, "batch kernel needs too much shared memory");
+        if ((st = load_variant(*B->module)) != CT_OK) return st;   // also fills in the register count
+        // problem table, tensor maps and work list: most expensive tiles first
+        // (solo problems keep zeroed entries that no work item names)
+        for (int i = 0; i < n; ++i) {
+            const int b = B->item_bucket[(size_t)i];
+            if (b < 0) {
+                probs.push_back(DevProblem{});
+                continue;
+            }
+            probs.push_back(dev_problem(*B, i, b, B->buckets[(size_t)b].cfg));
+            alignas(64) unsigned char map[kTensorMapBytes];
+            if ((st = item_map(*B, i, B->buckets[(size_t)b].cfg, map)) != CT_OK) return st;
+            memcpy(maps.data() + (size_t)i * kTensorMapBytes, map, kTensorMapBytes);
         }
+        std::vector<int> border(B->buckets.size());
+        std::iota(border.begin(), border.end(), 0);
+        auto tile_cost = [&](int b) {
+            const auto& k = B->buckets[(size_t)b];
+            return (double)k.fw * k.fh * tile_w(threads, k.cfg) * tile_h(threads, k.cfg);
+        };
+        std::stable_sort(border.begin(), border.end(), [&](int a, int b) { return tile_cost(a) > tile_cost(b); });
+        for (int b : border) {
+            std::vector<int> its = B->buckets[(size_t)b].items;
+            std::stable_sort(its.begin(), its.end(), [&](int a, int c) {
+                return (int64_t)items[a].out_w * items[a].out_h > (int64_t)items[c].out_w * items[c].out_h;
+            });
+            for (int i : its) {
+                const TileCfg& c = B->buckets[(size_t)b].cfg;
+                if (!tile_grid_ok(items[i].out_w, items[i].out_h, tile_w(threads, c), tile_h(threads, c)))
+                    return fail(CT_ERR_UNSUPPORTED, "batch item %d: more than %lld tiles along one side", i,
+                                (long long)kMaxTilesPerSide);
+                int64_t tx = 0;
+                const int64_t nt = tiles_of(items[i], threads, c, &tx);
+                for (int64_t k = 0; k < nt; ++k) work.push_back(work_item((uint32_t)i, k, tx));
+            }
+        }
+        if (work.size() > (size_t)0x7fffffff) return fail(CT_ERR_UNSUPPORTED, "too many tiles in one batch");
     }
-    if (work.size() > (size_t)0x7fffffff) return fail(CT_ERR_UNSUPPORTED, "too many tiles in one batch");
     B->n_work = (int64_t)work.size();
-    if ((e = cudaMalloc(&B->d_probs, probs.size() * sizeof(DevProblem))) != cudaSuccess ||
-        (e = cudaMalloc(&B->d_work, std::max<size_t>(1, work.size()) * sizeof(WorkItem))) != cudaSuccess ||
-        (e = cudaMalloc(&B->d_tmaps, maps.size())) != cudaSuccess ||
-        (e = cudaMalloc((void**)&B->d_counter, kCounterWords * sizeof(unsigned))) != cudaSuccess)
-        return cuda_fail(e, "cudaMalloc(batch tables)");
+    if ((e = cudaMalloc((void**)&B->d_counter, kCounterWords * sizeof(unsigned))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(batch counter)");
     cudaMemsetAsync(B->d_counter, 0, kCounterWords * sizeof(unsigned), s);
-    cudaMemcpyAsync(B->d_probs, probs.data(), probs.size() * sizeof(DevProblem), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(B->d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice, s);
-    if (!work.empty())
-        cudaMemcpyAsync(B->d_work, work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
+    if (persistent) {
+        if ((e = cudaMalloc(&B->d_probs, probs.size() * sizeof(DevProblem))) != cudaSuccess ||
+            (e = cudaMalloc(&B->d_work, std::max<size_t>(1, work.size()) * sizeof(WorkItem))) != cudaSuccess ||
+            (e = cudaMalloc(&B->d_tmaps, maps.size())) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(batch tables)");
+        cudaMemcpyAsync(B->d_probs, probs.data(), probs.size() * sizeof(DevProblem), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(B->d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice, s);
+        if (!work.empty())
+            cudaMemcpyAsync(B->d_work, work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
+        B->grid = occupancy_grid(*B->module, threads, o.blocks_per_sm, std::max<int64_t>(1, B->n_work));
+    }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "upload batch tables");
-    B->grid = occupancy_grid(*B->module, threads, o.blocks_per_sm, std::max<int64_t>(1, B->n_work));
-    // capture: counter reset + the persistent launch
-    DevParams prm{B->d_probs, B->d_work, B->d_filters, B->d_tmaps, B->d_counter, (int32_t)B->n_work, 0};
+    if (!device_error_word()) return fail(CT_ERR_CUDA, "no device error word");   // allocated before capture
+    // capture: the solo launches, then counter reset + the persistent launch
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamBeginCapture");
-    cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned), s);
-    st = launch_batch(*B->module, B->grid, threads, prm, s);
+    st = CT_OK;
+    for (size_t k = 0; k < B->solo_items.size() && st == CT_OK; ++k) {
+        const ct_batch_item& it = items[B->solo_items[k]];
+        const ct_problem p{it.out_w, it.out_h, it.filter_w, it.filter_h, it.in_pitch, it.out_pitch, o.dtype, 0};
+        st = launch_variant(*B->solo_vars[k], p, it.d_image, it.h_filter, it.d_out, s);
+    }
+    if (st == CT_OK && persistent) {
+        DevParams prm{B->d_probs, B->d_work, B->d_filters, B->d_tmaps, B->d_counter, (int32_t)B->n_work, 0};
+        cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned), s);
+        st = launch_batch(*B->module, B->grid, threads, prm, s);
+    }
     e = cudaStreamEndCapture(s, &g);
     if (st != CT_OK || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -543,9 +653,10 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
     B->info.n_work = B->n_work;
     B->info.grid = B->grid;
     B->info.threads = threads;
-    B->info.smem_bytes = (int32_t)B->module->smem;
-    B->info.regs = B->module->regs;
+    B->info.smem_bytes = persistent ? (int32_t)B->module->smem : 0;
+    B->info.regs = persistent ? B->module->regs : 0;
     B->info.compile_cpu_ms = compile_cpu;
+    B->info.n_solo = (int32_t)B->solo_items.size();
     B->info.plan_ms = now_ms() - t0;
     *out = B.release();
     return CT_OK;
@@ -566,6 +677,13 @@ CT_API ct_status ct_batch_check(const ct_batch* b)
     const cudaError_t e = cudaMemcpy(words, b->d_counter, sizeof words, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "read the batch status");
     if (words[1] & 1u) return fail(CT_ERR_TIMEOUT, "a block of an earlier run gave up waiting for its input copies");
+    if (!b->solo_items.empty()) {
+        unsigned* w = device_error_word();
+        unsigned dw = 0;
+        if (w && cudaMemcpy(&dw, w, 4, cudaMemcpyDeviceToHost) == cudaSuccess && (dw & 1u))
+            return fail(CT_ERR_TIMEOUT, "a single-problem launch on this device gave up waiting for its input copy");
+        cudaGetLastError();
+    }
     return CT_OK;
 }
 

@@ -102,7 +102,8 @@ def test_batch_workload_sampled(ctlib, cuda_device):
         probs.append((img, f, torch.from_numpy(img).to(cuda_device),
                       torch.empty((side, synthetic.round_up(side, 4)), device=cuda_device), side, fs))
     b = ctlib.Batch([(d, f, out, side + fs - 1) for (_, f, d, out, side, fs) in probs], tune=True,
-                    max_tune_items=3)
+                    max_tune_items=3, solo_evals=16)
+    assert b.info()["n_solo"] >= 1        # the largest problems run as their own launches
     b.run()
     torch.cuda.synchronize()
     b.check()
@@ -114,15 +115,17 @@ def test_batch_workload_sampled(ctlib, cuda_device):
 
 
 def test_tile_grid_limit(ctlib, cuda_device):
-    """A problem wider than 65535 tiles of any candidate tile is refused at
-    plan time (CT_ERR_UNSUPPORTED), tuned or not; no kernel runs."""
+    """In the persistent launch, a problem wider than 65535 tiles of any
+    candidate tile is refused at plan time (CT_ERR_UNSUPPORTED), tuned or
+    not; no kernel runs.  (By default such a problem fills the GPU and runs
+    as its own single-problem launch instead, which has no such limit.)"""
     ow = 1 << 24
     img = torch.zeros((1, ow), device=cuda_device)
     out = torch.empty((1, ow), device=cuda_device)
     f = np.ones((1, 1), np.float32)
     for tune in (True, False):
         with pytest.raises(ctlib.CTError) as e:
-            ctlib.Batch([(img, f, out, ow)], tune=tune)
+            ctlib.Batch([(img, f, out, ow)], tune=tune, solo_waves=-1)
         assert e.value.status == -8
 
 
@@ -151,3 +154,57 @@ def test_wait_timeout_is_reported(ctlib, cuda_device, monkeypatch):
     img, f, d, out, ow, oh, fw, fh = probs[0]
     ref, S = oracle.corr2d_f64(img, f, ow, oh)
     assert_parity(out[:oh, :ow].cpu().numpy(), ref, S, "batch after a timed-out run")
+
+
+def test_solo_problems_in_the_graph(ctlib, cuda_device):
+    """A problem that fills the GPU on its own (here: one wave) runs as its
+    own tuned single-problem launch in the plan's graph, the others in the
+    persistent launch; all outputs are bit-identical to the single-problem
+    kernel and match the oracle (sampled for the big one).  4500^2 outputs
+    exceed one wave under every configuration of the space (at most 65,536
+    outputs per block, at most 2,048 threads per SM)."""
+    shapes = [(4500, 4500, 17, 17), (300, 200, 17, 17), (513, 300, 11, 11), (64, 64, 3, 3)]
+    probs = _make(shapes, 12, cuda_device)
+    b = ctlib.Batch([(d, f, out, ow + fw - 1) for (_, f, d, out, ow, oh, fw, fh) in probs], tune=True,
+                    max_tune_items=3, solo_waves=1, solo_evals=12)
+    info = b.info()
+    assert info["n_solo"] == 1 and b.item_bucket(0) == -1
+    assert all(b.item_bucket(i) >= 0 for i in range(1, len(shapes)))
+    for rep in range(2):
+        b.run()
+        torch.cuda.synchronize()
+        b.check()
+        for k, (img, f, d, out, ow, oh, fw, fh) in enumerate(probs):
+            assert _guards_ok(out, ow, oh), (ow, oh, fw, fh)
+            got = out[:oh, :ow].cpu().numpy()
+            single = ctlib.conv2d(d, f, ctlib.config(32, 4, 4, 2, 1, 0), in_w=ow + fw - 1)
+            torch.cuda.synchronize()
+            assert np.array_equal(got.view(np.uint32), single.cpu().numpy().view(np.uint32)), k
+            if k == 0:
+                xs, ys = synthetic.sample_points(7, ow, oh, 2000)
+                ref, S = oracle.corr2d_points(img, f, xs, ys)
+                assert np.all(np.abs(got[ys, xs].astype(np.float64) - ref) <= 1e-5 * S)
+            else:
+                ref, S = oracle.corr2d_f64(img, f, ow, oh)
+                assert_parity(got, ref, S, f"batch {ow}x{oh} f{fw}x{fh}")
+            out[:oh, :ow].fill_(float("nan"))
+
+
+def test_every_problem_solo(ctlib, cuda_device):
+    """With every problem big enough to go solo the graph holds no
+    persistent launch; results still match the single-problem kernel."""
+    shapes = [(4500, 4500, 5, 5), (4600, 4500, 5, 5)]
+    probs = _make(shapes, 13, cuda_device)
+    b = ctlib.Batch([(d, f, out, ow + fw - 1) for (_, f, d, out, ow, oh, fw, fh) in probs], tune=False,
+                    solo_waves=1, solo_evals=8)
+    info = b.info()
+    assert info["n_solo"] == 2 and info["n_buckets"] == 0 and info["n_work"] == 0
+    b.run()
+    torch.cuda.synchronize()
+    b.check()
+    for (img, f, d, out, ow, oh, fw, fh) in probs:
+        got = out[:oh, :ow].cpu().numpy()
+        single = ctlib.conv2d(d, f, ctlib.config(16, 16, 4, 2, 1, 1), in_w=ow + fw - 1)
+        torch.cuda.synchronize()
+        assert np.array_equal(got.view(np.uint32), single.cpu().numpy().view(np.uint32))
+        assert _guards_ok(out, ow, oh)
