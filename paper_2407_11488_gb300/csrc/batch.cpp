@@ -624,15 +624,47 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
     }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "upload batch tables");
     if (!device_error_word()) return fail(CT_ERR_CUDA, "no device error word");   // allocated before capture
-    // capture: the solo launches, then counter reset + the persistent launch
+    // capture: the solo launches spread over up to three forked streams (their
+    // ramps and tails overlap), joined, then counter reset + the persistent
+    // launch.  The fork streams and events live only for the capture.
+    const size_t nfs = std::min<size_t>(3, B->solo_items.size());
+    struct Forks {
+        std::vector<cudaStream_t> streams;
+        std::vector<cudaEvent_t> events;
+        ~Forks()
+        {
+            for (auto x : streams) cudaStreamDestroy(x);
+            for (auto x : events) cudaEventDestroy(x);
+        }
+    } forks;
+    for (size_t k = 0; k < nfs + 1; ++k) {
+        cudaEvent_t ev = nullptr;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventCreate");
+        forks.events.push_back(ev);
+    }
+    for (size_t k = 0; k < nfs; ++k) {
+        cudaStream_t x = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreate");
+        forks.streams.push_back(x);
+    }
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamBeginCapture");
     st = CT_OK;
-    for (size_t k = 0; k < B->solo_items.size() && st == CT_OK; ++k) {
-        const ct_batch_item& it = items[B->solo_items[k]];
-        const ct_problem p{it.out_w, it.out_h, it.filter_w, it.filter_h, it.in_pitch, it.out_pitch, o.dtype, 0};
-        st = launch_variant(*B->solo_vars[k], p, it.d_image, it.h_filter, it.d_out, s);
+    if (nfs > 0) {
+        cudaEventRecord(forks.events[0], s);
+        for (size_t k = 0; k < nfs; ++k) cudaStreamWaitEvent(forks.streams[k], forks.events[0], 0);
+        for (size_t k = 0; k < B->solo_items.size() && st == CT_OK; ++k) {
+            const ct_batch_item& it = items[B->solo_items[k]];
+            const ct_problem p{it.out_w, it.out_h, it.filter_w, it.filter_h, it.in_pitch, it.out_pitch, o.dtype, 0};
+            st = launch_variant(*B->solo_vars[k], p, it.d_image, it.h_filter, it.d_out, forks.streams[k % nfs]);
+        }
+        for (size_t k = 0; k < nfs; ++k) {
+            cudaEventRecord(forks.events[k + 1], forks.streams[k]);
+            cudaStreamWaitEvent(s, forks.events[k + 1], 0);
+        }
     }
     if (st == CT_OK && persistent) {
         DevParams prm{B->d_probs, B->d_work, B->d_filters, B->d_tmaps, B->d_counter, (int32_t)B->n_work, 0};
