@@ -57,7 +57,7 @@ struct CtBatchProblem {
     float* out;
     ct_i64 in_pitch, out_pitch;
     int out_w, out_h, in_w, in_h;
-    int bucket, tiles_x, filt_off, pad;
+    int bucket, tiles_x, filt_off, pad;   // tiles_x: tile columns (for inspection; work items carry their tile)
 };
 
 struct CtBatchParams {

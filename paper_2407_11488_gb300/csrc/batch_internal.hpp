@@ -20,7 +20,7 @@ struct DevProblem {
     float* out;
     int64_t in_pitch, out_pitch;
     int32_t out_w, out_h, in_w, in_h;
-    int32_t bucket, tiles_x, filt_off, pad;
+    int32_t bucket, tiles_x, filt_off, pad;   // tiles_x is for inspection: work items carry their tile
 };
 static_assert(sizeof(DevProblem) == 64, "DevProblem layout");
 struct DevParams {

@@ -90,9 +90,7 @@ struct CtParams {
 #define CT_TILE_H (CT_BY * CT_TY)
 #define CT_HALO_W (CT_TILE_W + CT_FW - 1)
 #define CT_HALO_H (CT_TILE_H + CT_FH - 1)
-#define CT_SW (((CT_HALO_W + 3) / 4) * 4)
-#define CT_ESZ (CT_DTYPE == 0 ? 4 : 2)
-#define CT_SWT (((CT_HALO_W + 16 / CT_ESZ - 1) / (16 / CT_ESZ)) * (16 / CT_ESZ))   // tensor-copy box width
+#define CT_SW (((CT_HALO_W + 3) / 4) * 4)   // staged row length in floats (the tensor-copy box width)
 
 #if CT_TX % 4 == 0
 #define CT_VW 4
@@ -184,23 +182,6 @@ __device__ __forceinline__ bool ct_bar_wait(unsigned long long* bar, unsigned pa
     }
 }
 
-// One input row of the thread's window from the tensor-copied halo (CT_SWT
-// floats per row).
-__device__ __forceinline__ void ct_row_staged(float (&w)[CT_WWV], const float* __restrict__ s)
-{
-#pragma unroll
-    for (int k = 0; k < CT_WWV; k += CT_VW) {
-        if (CT_VW == 4) {
-            const float4 v = *reinterpret_cast<const float4*>(s + k);
-            w[k] = v.x; w[k + 1] = v.y; w[k + 2] = v.z; w[k + 3] = v.w;
-        } else if (CT_VW == 2) {
-            const float2 v = *reinterpret_cast<const float2*>(s + k);
-            w[k] = v.x; w[k + 1] = v.y;
-        } else {
-            w[k] = s[k];
-        }
-    }
-}
 #endif
 
 __device__ __forceinline__ void ct_row_shared(float (&w)[CT_WWV], const float* __restrict__ s)
@@ -239,7 +220,7 @@ ct_corr2d(const __grid_constant__ CtParams p)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(ct_sa(&ct_bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(ct_sa(&ct_bar)),
-                     "r"((unsigned)(CT_HALO_H * CT_SWT * CT_ESZ + CT_TEST_EXTRA_TX))
+                     "r"((unsigned)(CT_HALO_H * CT_SW * 4 + CT_TEST_EXTRA_TX))
                      : "memory");
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
@@ -255,7 +236,7 @@ ct_corr2d(const __grid_constant__ CtParams p)
         }
         return;
     }
-#define CT_LOAD_ROW(w, r) ct_row_staged(w, sm + (ly + (r)) * CT_SWT + lx)
+#define CT_LOAD_ROW(w, r) ct_row_shared(w, sm + (ly + (r)) * CT_SW + lx)
 #elif CT_SMEM
     extern __shared__ float4 ct_smem4[];
     float* sm = reinterpret_cast<float*>(ct_smem4);
