@@ -192,9 +192,37 @@ def cpu_baseline(img, f, out_w, out_h, seconds):
         done_rows += rows
         reps += 1
     flops = 2.0 * done_rows * out_w * fw * fh
-    return {"value": flops / t_total / 1e9, "unit": "GFLOP/s", "cores": oracle.max_threads(), "kind": "oracle",
+    cores = oracle.max_threads()
+    # one thread, on a band sized to about three seconds
+    rows1 = int(max(1, min(out_h, 3.0 / max(dt0 * cores / 16, 1e-6))))
+    t = time.perf_counter()
+    oracle.corr2d_f64(img[0:rows1 + fh - 1], f, out_w, rows1, nthreads=1)
+    t1 = time.perf_counter() - t
+    return {"value": flops / t_total / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
             "sample": f"{reps} bands of {rows} output rows x {out_w} cols (filter {fw}x{fh}) of the "
-                      f"{out_w}x{out_h} workload, {t_total:.1f} s of FP64 CPU work"}
+                      f"{out_w}x{out_h} workload, {t_total:.1f} s of FP64 CPU work",
+            "value_1thread": 2.0 * rows1 * out_w * fw * fh / t1 / 1e9,
+            "sample_1thread": f"{rows1} output rows x {out_w} cols, {t1:.1f} s", "cpu_model": cpu_model()}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args):
@@ -312,6 +340,7 @@ def run_ours(args):
     # ---- tuning (before the timed region)
     tuning = {}
     analysis = {}
+    tab = None
     if args.config:
         best = ct.config(*[int(v) for v in args.config.split(",")])
         n_valid = ct.Space(space).count(p)[1]
@@ -483,6 +512,16 @@ def run_ours(args):
         oracle.build()
         f_np = f.float().numpy() if hasattr(f, "float") else f
         line["cpu_baseline"] = cpu_baseline(img, f_np, ow, oh, args.cpu_seconds)
+        if tab is not None:
+            # the oracle's exhaustive CPU-side ranking of the same timing table
+            from oracle import analysis as oan
+            rows = [{"index": r["index"], "status": r["status"], "t": r["t_med_ms"]} for r in tab.rows]
+            t = time.perf_counter()
+            ost = oan.stats(rows, flops)
+            line["cpu_baseline"]["ranking"] = {
+                "rows": len(rows), "ms": (time.perf_counter() - t) * 1e3,
+                "same_optimum_as_the_tuner": ost is not None and
+                ost["best_index"] == tab.rows[tab.info["best_row"]]["index"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
