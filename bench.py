@@ -69,8 +69,9 @@ def parse():
                     help="skip: time only the batched path (profiling)")
     ap.add_argument("--batch-plain-evals", type=int, default=120,
                     help="annealing budget per filter size for the per-problem path of the batch workload")
-    ap.add_argument("--batch-solo-waves", type=int, default=0,
-                    help="batch: problems filling this many GPU waves run as their own launch (0: library default)")
+    ap.add_argument("--batch-solo-pct", type=int, default=0,
+                    help="batch: problems filling this percentage of a GPU wave run as their own launch "
+                         "(0: library default; < 0: none)")
     ap.add_argument("--strategy", choices=["random", "anneal", "brute"], default="brute",
                     help="tuning strategy of the timed configuration (brute: the exhaustive optimum)")
     ap.add_argument("--extra-strategies", default="", help="comma list also run (wall time reported)")
@@ -598,12 +599,12 @@ def run_batch(args):
 
     t0 = time.time()
     batch = ct.Batch([(d_img, f, out, side + fs - 1) for (_, f, d_img, out, side, fs) in probs], tune=True,
-                     max_tune_items=6, solo_waves=args.batch_solo_waves)
+                     max_tune_items=6, solo_wave_pct=args.batch_solo_pct)
     batch_plan_s = time.time() - t0
     binfo = batch.info()
     # the same plan with every problem in the persistent launch (no solo launches)
     persistent = ct.Batch([(d_img, f, out, side + fs - 1) for (_, f, d_img, out, side, fs) in probs], tune=True,
-                          max_tune_items=6, solo_waves=-1) if binfo["n_solo"] else batch
+                          max_tune_items=6, solo_wave_pct=-1) if binfo["n_solo"] else batch
 
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(int(2 * max(info.l2_bytes, 64 << 20)), dtype=torch.uint8, device=dev)

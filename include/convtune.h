@@ -337,12 +337,14 @@ CT_API ct_status ct_table_analyze(const ct_table* t, const ct_space* s, double f
  * Eq. 3), the alternative the bucket's summed time.  Results are bit-identical
  * to ct_conv2d on each problem.
  *
- * Problems big enough to fill the GPU on their own (opts->solo_waves) run
- * instead as their own launch of the single-problem kernel, whose taps are
+ * Problems big enough to fill a good part of the GPU (opts->solo_wave_pct)
+ * run instead as their own launch of the single-problem kernel, whose taps are
  * constant-bank operands; its configuration is tuned per filter size at
  * create (annealing, opts->solo_evals evaluations, on the largest such
  * problem, whose buffers the tuner uses).  The plan's graph holds these
- * launches first, then the persistent launch of the other problems.
+ * launches, largest first, spread over opts->solo_branches parallel branches
+ * (so small ones run beside each other), then the persistent launch of the
+ * other problems.
  *
  * Each item's input halo and filter taps reach shared memory by tensor-memory
  * copies (one 2D tensor map per problem, encoded at create for the bucket's
@@ -373,11 +375,11 @@ typedef struct {
     int32_t side_split;     /* image side splitting a filter size into two buckets (0: 512; < 0: no split) */
     int32_t blocks_per_sm;  /* resident blocks per SM of the persistent grid (0: occupancy query) */
     int32_t max_tune_items; /* problems per bucket measured while tuning (0: 12) */
-    int32_t solo_waves;     /* a problem whose tiles under its solo configuration fill at least this many
-                               waves of the GPU runs as its own ct_corr2d launch in the plan's graph
-                               (0: 1; < 0: every problem goes to the persistent launch) */
+    int32_t solo_wave_pct;  /* a problem whose tiles under its solo configuration fill at least this
+                               percentage of one wave of the GPU runs as its own ct_corr2d launch in the
+                               plan's graph (0: 10; < 0: every problem goes to the persistent launch) */
     int32_t solo_evals;     /* annealing budget per filter size for the solo configuration (0: 60) */
-    int32_t reserved;
+    int32_t solo_branches;  /* parallel graph branches the solo launches are spread over (0: 12) */
 } ct_batch_opts;
 
 typedef struct {

@@ -99,8 +99,8 @@ class BucketConfig(ctypes.Structure):
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("dtype", i32), ("threads", i32), ("tune", i32), ("objective", i32), ("side_split", i32),
-                ("blocks_per_sm", i32), ("max_tune_items", i32), ("solo_waves", i32), ("solo_evals", i32),
-                ("reserved", i32)]
+                ("blocks_per_sm", i32), ("max_tune_items", i32), ("solo_wave_pct", i32), ("solo_evals", i32),
+                ("solo_branches", i32)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -534,8 +534,9 @@ def tune_replay(problem: Problem, space, strategy, times_ms, **opts) -> Table:
 class Batch:
     """Many uneven correlations in one graph launch (ct_batch_*): a
     persistent launch over all problems, except those that fill at least
-    ``solo_waves`` waves of the GPU (0: 1; < 0: none), which run as their
-    own launch of the single-problem kernel.
+    ``solo_wave_pct`` percent of one wave of the GPU (0: 10; < 0: none),
+    which run as their own launches of the single-problem kernel, spread over
+    ``solo_branches`` parallel graph branches (0: 12).
 
     ``problems`` is a list of (image, filt, out, in_w): CUDA image tensor
     (in_h, in_pitch) with in_w valid columns, host filter (fh, fw), CUDA
@@ -543,7 +544,7 @@ class Batch:
     alive while the batch is used; filters are copied at creation."""
 
     def __init__(self, problems, *, dtype=None, threads=256, tune=True, objective="pp", side_split=512,
-                 blocks_per_sm=0, max_tune_items=12, solo_waves=0, solo_evals=0):
+                 blocks_per_sm=0, max_tune_items=12, solo_wave_pct=0, solo_evals=0, solo_branches=0):
         import torch
         self._keep = []
         arr = (BatchItem * len(problems))()
@@ -560,7 +561,7 @@ class Batch:
             arr[k] = BatchItem(img.data_ptr(), out.data_ptr(), fb.ctypes.data, p.out_w, p.out_h, p.filter_w,
                                p.filter_h, p.in_pitch, out.stride(0))
         o = BatchOpts(dt if dtype is None else dtype, threads, int(tune), 1 if objective == "time" else 0,
-                      side_split, blocks_per_sm, max_tune_items, solo_waves, solo_evals, 0)
+                      side_split, blocks_per_sm, max_tune_items, solo_wave_pct, solo_evals, solo_branches)
         h = vp()
         _check(_load().ct_batch_create(arr, len(problems), ctypes.byref(o), ctypes.byref(h)))
         self.handle = h

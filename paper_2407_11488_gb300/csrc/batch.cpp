@@ -363,16 +363,16 @@ ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o,
     return CT_OK;
 }
 
-// Problems that fill at least `waves` waves of the GPU on their own go solo.
-// For every filter size whose largest problem could (one output per resident
-// thread and wave), the single-problem configuration is tuned on that
+// Problems that fill at least `pct` percent of one wave of the GPU on their
+// own go solo.  For every filter size whose largest problem could (one output
+// per resident thread), the single-problem configuration is tuned on that
 // problem (annealing, o.solo_evals evaluations, on its own buffers); each
 // problem of that size whose tile count under the configuration reaches
-// waves x SMs x resident blocks then runs as its own launch of it.
+// pct/100 x SMs x resident blocks then runs as its own launch of it.
 ct_status plan_solo(ct_batch& B, const ct_batch_opts& o, std::vector<char>& solo, double* tune_ms)
 {
-    const int waves = o.solo_waves == 0 ? 1 : o.solo_waves;
-    if (waves <= 0) return CT_OK;
+    const int pct = o.solo_wave_pct == 0 ? 10 : o.solo_wave_pct;
+    if (pct <= 0) return CT_OK;
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -380,7 +380,7 @@ ct_status plan_solo(ct_batch& B, const ct_batch_opts& o, std::vector<char>& solo
     auto area = [&](int i) { return (int64_t)B.items[(size_t)i].out_w * B.items[(size_t)i].out_h; };
     std::map<std::pair<int, int>, int> largest;
     for (int i = 0; i < n; ++i) {
-        if (area(i) < (int64_t)waves * sms * 2048) continue;
+        if (area(i) * 100 < (int64_t)pct * sms * 2048) continue;
         const auto key = std::make_pair(B.items[(size_t)i].filter_w, B.items[(size_t)i].filter_h);
         auto f = largest.find(key);
         if (f == largest.end() || area(i) > area(f->second)) largest[key] = i;
@@ -421,7 +421,7 @@ ct_status plan_solo(ct_batch& B, const ct_batch_opts& o, std::vector<char>& solo
             cudaGetLastError();
             nb = 1;
         }
-        const int64_t slots = (int64_t)waves * sms * nb;
+        const int64_t slots = std::max<int64_t>(1, (int64_t)pct * sms * nb / 100);
         const int64_t tw = (int64_t)best.block_x * best.tile_x, th = (int64_t)best.block_y * best.tile_y;
         for (int i = 0; i < n; ++i) {
             const ct_batch_item& it = B.items[(size_t)i];
@@ -624,10 +624,11 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
     }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "upload batch tables");
     if (!device_error_word()) return fail(CT_ERR_CUDA, "no device error word");   // allocated before capture
-    // capture: the solo launches spread over up to three forked streams (their
-    // ramps and tails overlap), joined, then counter reset + the persistent
-    // launch.  The fork streams and events live only for the capture.
-    const size_t nfs = std::min<size_t>(3, B->solo_items.size());
+    // capture: the solo launches spread round-robin over forked streams (their
+    // ramps and tails overlap, small ones run side by side), joined, then
+    // counter reset + the persistent launch.  The fork streams and events live
+    // only for the capture.
+    const size_t nfs = std::min<size_t>(o.solo_branches > 0 ? (size_t)o.solo_branches : 12, B->solo_items.size());
     struct Forks {
         std::vector<cudaStream_t> streams;
         std::vector<cudaEvent_t> events;

@@ -469,7 +469,7 @@ CT_API ct_status ct_server_create(const ct_server_opts* opts, ct_server** out)
         bo.dtype = o.dtype;
         bo.tune = 1;
         bo.side_split = -1;
-        bo.solo_waves = -1;   // every representative problem tunes its bucket
+        bo.solo_wave_pct = -1;   // every representative problem tunes its bucket
         ct_batch* tb = nullptr;
         st = ct_batch_create(items.data(), (int32_t)items.size(), &bo, &tb);
         if (st == CT_OK) {

@@ -51,7 +51,7 @@ SHAPES = [(700, 650, 17, 17), (513, 300, 11, 11), (128, 128, 3, 3), (1, 1, 5, 5)
 def test_batch_matches_oracle_and_single_kernel(ctlib, cuda_device, tune):
     probs = _make(SHAPES, 3, cuda_device)
     b = ctlib.Batch([(d, f, out, ow + fw - 1) for (_, f, d, out, ow, oh, fw, fh) in probs], tune=tune,
-                    max_tune_items=4)
+                    max_tune_items=4, solo_wave_pct=-1)        # every problem in the persistent launch
     info = b.info()
     assert info["n_items"] == len(SHAPES) and info["n_work"] > 0 and info["grid"] > 0
     for rep in range(2):       # the graph is replayable
@@ -80,7 +80,8 @@ def test_batch_matches_oracle_and_single_kernel(ctlib, cuda_device, tune):
 def test_batch_bf16(ctlib, cuda_device):
     shapes = [(300, 200, 9, 9), (1024, 64, 17, 17), (50, 77, 3, 5)]
     probs = _make(shapes, 4, cuda_device, dtype=torch.bfloat16)
-    b = ctlib.Batch([(d, f, out, ow + fw - 1) for (_, f, d, out, ow, oh, fw, fh) in probs], tune=False)
+    b = ctlib.Batch([(d, f, out, ow + fw - 1) for (_, f, d, out, ow, oh, fw, fh) in probs], tune=False,
+                    solo_wave_pct=-1)
     b.run()
     torch.cuda.synchronize()
     b.check()
@@ -125,7 +126,7 @@ def test_tile_grid_limit(ctlib, cuda_device):
     f = np.ones((1, 1), np.float32)
     for tune in (True, False):
         with pytest.raises(ctlib.CTError) as e:
-            ctlib.Batch([(img, f, out, ow)], tune=tune, solo_waves=-1)
+            ctlib.Batch([(img, f, out, ow)], tune=tune, solo_wave_pct=-1)
         assert e.value.status == -8
 
 
@@ -137,7 +138,7 @@ def test_wait_timeout_is_reported(ctlib, cuda_device, monkeypatch):
     probs = _make([(64, 64, 3, 3)], 9, cuda_device)
     items = [(d, f, out, ow + fw - 1) for (_, f, d, out, ow, oh, fw, fh) in probs]
     monkeypatch.setenv("CONVTUNE_NVRTC_EXTRA", "-DCT_TEST_EXTRA_TX=16")
-    bad = ctlib.Batch(items, tune=False)
+    bad = ctlib.Batch(items, tune=False, solo_wave_pct=-1)
     monkeypatch.delenv("CONVTUNE_NVRTC_EXTRA")
     t0 = time.time()
     bad.run()
@@ -147,7 +148,7 @@ def test_wait_timeout_is_reported(ctlib, cuda_device, monkeypatch):
         bad.check()
     assert e.value.status == -7
     del bad
-    good = ctlib.Batch(items, tune=False)
+    good = ctlib.Batch(items, tune=False, solo_wave_pct=-1)
     good.run()
     torch.cuda.synchronize()
     good.check()
@@ -166,7 +167,7 @@ def test_solo_problems_in_the_graph(ctlib, cuda_device):
     shapes = [(4500, 4500, 17, 17), (300, 200, 17, 17), (513, 300, 11, 11), (64, 64, 3, 3)]
     probs = _make(shapes, 12, cuda_device)
     b = ctlib.Batch([(d, f, out, ow + fw - 1) for (_, f, d, out, ow, oh, fw, fh) in probs], tune=True,
-                    max_tune_items=3, solo_waves=1, solo_evals=12)
+                    max_tune_items=3, solo_wave_pct=100, solo_evals=12)
     info = b.info()
     assert info["n_solo"] == 1 and b.item_bucket(0) == -1
     assert all(b.item_bucket(i) >= 0 for i in range(1, len(shapes)))
@@ -196,7 +197,7 @@ def test_every_problem_solo(ctlib, cuda_device):
     shapes = [(4500, 4500, 5, 5), (4600, 4500, 5, 5)]
     probs = _make(shapes, 13, cuda_device)
     b = ctlib.Batch([(d, f, out, ow + fw - 1) for (_, f, d, out, ow, oh, fw, fh) in probs], tune=False,
-                    solo_waves=1, solo_evals=8)
+                    solo_wave_pct=100, solo_evals=8)
     info = b.info()
     assert info["n_solo"] == 2 and info["n_buckets"] == 0 and info["n_work"] == 0
     b.run()
