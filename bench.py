@@ -69,6 +69,8 @@ def parse():
                     help="skip: time only the batched path (profiling)")
     ap.add_argument("--batch-plain-evals", type=int, default=120,
                     help="annealing budget per filter size for the per-problem path of the batch workload")
+    ap.add_argument("--batch-solo-branches", type=int, default=0,
+                    help="batch: parallel graph branches of the solo launches (0: library default)")
     ap.add_argument("--batch-solo-pct", type=int, default=0,
                     help="batch: problems filling this percentage of a GPU wave run as their own launch "
                          "(0: library default; < 0: none)")
@@ -599,7 +601,7 @@ def run_batch(args):
 
     t0 = time.time()
     batch = ct.Batch([(d_img, f, out, side + fs - 1) for (_, f, d_img, out, side, fs) in probs], tune=True,
-                     max_tune_items=6, solo_wave_pct=args.batch_solo_pct)
+                     max_tune_items=6, solo_wave_pct=args.batch_solo_pct, solo_branches=args.batch_solo_branches)
     batch_plan_s = time.time() - t0
     binfo = batch.info()
     # the same plan with every problem in the persistent launch (no solo launches)
