@@ -255,7 +255,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_row * oh,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"corr2d {ow}x{oh} f{fs}x{fs} seed {seed}",
+            "data": "synthetic", "config": {"workload": f"corr2d out {ow}x{oh}, filter {fs}x{fs}, uniform[-1,1) seed {seed}",
                                            "note": "ms_per_step scaled to one full-size correlation"},
             "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": oracle.max_threads(), "kind": "oracle",
                              "sample": sample},
