@@ -407,9 +407,10 @@ ct_status plan_solo(ct_batch& B, const ct_batch_opts& o, std::vector<char>& solo
         ct_table* t = nullptr;
         st = ct_tune(&p, sp, CT_ANNEAL, &to, big.d_image, big.h_filter, big.d_out, &best, &t);
         if (t) ct_table_free(t);
-        if (st != CT_OK)
+        if (st == CT_ERR_CUDA)
             return fail(st, "tuning the single-problem configuration for filter %dx%d: %s", big.filter_w,
                         big.filter_h, last_error());
+        if (st != CT_OK) continue;   // no configuration ran: this size stays in the persistent launch
         VariantPtr v = compile_variant(VariantKey{best, big.filter_w, big.filter_h, B.dtype}, cache_dir_setting());
         if (!v || v->status != CT_OK)
             return fail(CT_ERR_COMPILE, "single-problem variant: %s", v ? v->error.c_str() : "no variant");
