@@ -710,7 +710,7 @@ def run_batch(args):
         "e2e": {"value": world * flops / te / 1e9, "unit": "GFLOP/s",
                 "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in h_imgs)),
                 "d2h_bytes_per_step": int(sum(h.numel() * 4 for h in h_outs)), "ms_per_step": te * 1e3},
-        "gpu_launches": k,
+        "gpu_launches": k * (binfo["n_solo"] + (1 if binfo["n_work"] > 0 else 0)),
         "clocks": clocks.summary(tb0, tb1),
         "device": info.name.decode(),
     }
