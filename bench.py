@@ -851,6 +851,7 @@ def run_serve(args):
         "server_create_s": create_s,
         "plain_configs": {str(k): v.as_dict() for k, v in cfg.items()},
         "e2e": {"value": served_gflops, "unit": "GFLOP/s", "note": "host buffers in and out for every request"},
+        "gpu_launches": st_sat["launches"],
         "device": info.name.decode(),
     }
     print(json.dumps(line), flush=True)
