@@ -209,3 +209,33 @@ def test_every_problem_solo(ctlib, cuda_device):
         torch.cuda.synchronize()
         assert np.array_equal(got.view(np.uint32), single.cpu().numpy().view(np.uint32))
         assert _guards_ok(out, ow, oh)
+
+
+def test_bf16_plan_with_a_solo_problem(ctlib, cuda_device):
+    """BF16 storage through a plan that holds a solo launch (4500^2, one wave)
+    and a persistent launch (a small problem): bit-identical to the
+    single-problem kernel, and within 1e-5 * S of the oracle on the
+    BF16-rounded values (widened exactly to FP32; sampled for the big one)."""
+    shapes = [(4500, 4500, 5, 5), (300, 200, 9, 9)]
+    probs = _make(shapes, 14, cuda_device, dtype=torch.bfloat16)
+    b = ctlib.Batch([(d, f, out, ow + fw - 1) for (_, f, d, out, ow, oh, fw, fh) in probs], tune=False,
+                    solo_wave_pct=100, solo_evals=8)
+    assert b.info()["n_solo"] == 1 and b.item_bucket(0) == -1 and b.item_bucket(1) >= 0
+    b.run()
+    torch.cuda.synchronize()
+    b.check()
+    for k, (img, f, d, out, ow, oh, fw, fh) in enumerate(probs):
+        assert _guards_ok(out, ow, oh)
+        got = out[:oh, :ow].cpu().numpy()
+        single = ctlib.conv2d(d, f, ctlib.config(32, 4, 4, 2, 1, 0), in_w=ow + fw - 1)
+        torch.cuda.synchronize()
+        assert np.array_equal(got.view(np.uint32), single.cpu().numpy().view(np.uint32)), k
+        img_b = torch.from_numpy(img).to(torch.bfloat16).float().numpy()
+        f_b = f.float().numpy()
+        if k == 0:
+            xs, ys = synthetic.sample_points(9, ow, oh, 2000)
+            ref, S = oracle.corr2d_points(img_b, f_b, xs, ys)
+            assert np.all(np.abs(got[ys, xs].astype(np.float64) - ref) <= 1e-5 * S)
+        else:
+            ref, S = oracle.corr2d_f64(img_b, f_b, ow, oh)
+            assert_parity(got, ref, S, "bf16 persistent part")
