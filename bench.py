@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch", "serve"], default="full")
     ap.add_argument("--requests", type=int, default=100000, help="serve: requests of the Poisson stream")
     ap.add_argument("--sat-requests", type=int, default=20000, help="serve: requests of the saturation runs")
-    ap.add_argument("--anneal-chains", type=int, default=4)
+    ap.add_argument("--anneal-chains", type=int, default=16)
     ap.add_argument("--batch-filter", type=int, default=0,
                     help="batch: keep only the problems with this filter size (diagnostics)")
     ap.add_argument("--batch-plain", choices=["tune", "skip"], default="tune",

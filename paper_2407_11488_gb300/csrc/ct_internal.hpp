@@ -165,7 +165,9 @@ cudaError_t launch_l2_flush(void* buf, int64_t bytes, uint32_t salt, cudaStream_
 class CompilePool {
 public:
     using Job = std::function<VariantPtr()>;
-    CompilePool(int nthreads, std::string cache_dir);
+    // reserve_urgent threads are kept for urgent requests: speculative jobs
+    // run on at most threads - reserve_urgent of them at a time.
+    CompilePool(int nthreads, std::string cache_dir, int reserve_urgent = 0);
     ~CompilePool();
     // urgent requests go to the front of the queue (or move there if queued)
     std::shared_future<VariantPtr> request(const VariantKey& k, bool urgent = false);
@@ -180,6 +182,7 @@ private:
         uint64_t key;
         Job job;
         std::shared_ptr<std::promise<VariantPtr>> pr;
+        bool urgent = false;
     };
     void worker();
     std::string cache_dir_;
@@ -188,6 +191,7 @@ private:
     std::deque<Item> queue_;
     std::unordered_map<uint64_t, std::shared_future<VariantPtr>> futures_;
     std::vector<std::thread> threads_;
+    size_t max_speculative_ = 0, running_speculative_ = 0;
     bool stop_ = false;
 };
 

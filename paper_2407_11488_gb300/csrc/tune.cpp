@@ -14,9 +14,10 @@
 namespace ct {
 
 // ---------------------------------------------------------- compile pool ---
-CompilePool::CompilePool(int nthreads, std::string cache_dir) : cache_dir_(std::move(cache_dir))
+CompilePool::CompilePool(int nthreads, std::string cache_dir, int reserve_urgent) : cache_dir_(std::move(cache_dir))
 {
     if (nthreads <= 0) nthreads = (int)std::max(1u, std::thread::hardware_concurrency());
+    max_speculative_ = (size_t)std::max(1, nthreads - std::max(0, reserve_urgent));
     for (int i = 0; i < nthreads; ++i) threads_.emplace_back([this] { worker(); });
 }
 
@@ -47,8 +48,10 @@ std::shared_future<VariantPtr> CompilePool::request(uint64_t key, Job job, bool 
             for (auto q = queue_.begin(); q != queue_.end(); ++q)
                 if (q->key == key) {
                     Item item = *q;
+                    item.urgent = true;
                     queue_.erase(q);
                     queue_.push_front(item);
+                    cv_.notify_all();
                     break;
                 }
         }
@@ -57,10 +60,10 @@ std::shared_future<VariantPtr> CompilePool::request(uint64_t key, Job job, bool 
     auto pr = std::make_shared<std::promise<VariantPtr>>();
     auto fut = pr->get_future().share();
     futures_[key] = fut;
-    Item item{key, std::move(job), pr};
+    Item item{key, std::move(job), pr, urgent};
     if (urgent) queue_.push_front(std::move(item));
     else queue_.push_back(std::move(item));
-    cv_.notify_one();
+    cv_.notify_all();
     return fut;
 }
 
@@ -84,12 +87,21 @@ void CompilePool::worker()
         Item job;
         {
             std::unique_lock<std::mutex> g(mu_);
-            cv_.wait(g, [this] { return stop_ || !queue_.empty(); });
+            cv_.wait(g, [this] {
+                return stop_ ||
+                       (!queue_.empty() && (queue_.front().urgent || running_speculative_ < max_speculative_));
+            });
             if (stop_) return;
             job = queue_.front();
             queue_.pop_front();
+            if (!job.urgent) ++running_speculative_;
         }
         job.pr->set_value(job.job());
+        if (!job.urgent) {
+            std::lock_guard<std::mutex> g(mu_);
+            --running_speculative_;
+            cv_.notify_all();
+        }
     }
 }
 
@@ -177,7 +189,7 @@ public:
         Measure m;
         const VariantKey k = key(e);
         const double t0 = now_ms();
-        VariantPtr v = pool_.request(k).get();
+        VariantPtr v = pool_.request(k, true).get();   // needed now
         compile_wait_ms += now_ms() - t0;
         pool_.forget(k);
         if (!v) {
@@ -802,7 +814,11 @@ ct_status tune_gpu(const ct_problem* p, const ct_space* s, ct_strategy st, const
     int threads = o.compile_threads > 0 ? o.compile_threads : (int)std::max(1u, std::thread::hardware_concurrency());
     auto* t = new ct_table();
     {
-        CompilePool pool(threads, o.cache_dir ? std::string(o.cache_dir) : cache_dir_setting());
+        // annealing compiles its walkers' candidates urgently and their
+        // neighbours speculatively: a quarter of the threads stay free for
+        // the urgent ones, so a candidate never waits behind slow guesses
+        CompilePool pool(threads, o.cache_dir ? std::string(o.cache_dir) : cache_dir_setting(),
+                         st == CT_ANNEAL ? std::max(1, threads / 4) : 0);
         GpuEvaluator ev(*p, to, img, h_filter, out, pool, flush, flush_bytes, stream);
         rc = run_strategy(*p, s->s, st, o, valid, ev, *t, 2 * threads + 4);
         if (rc == CT_OK && ev.fatal != CT_OK) rc = ev.fatal;
