@@ -324,10 +324,10 @@ CT_API ct_status ct_table_analyze(const ct_table* t, const ct_space* s, double f
                                   int32_t n_p, ct_analysis* out);
 
 
-/* ---- batched uneven problems (one persistent launch) ---------------------
+/* ---- batched uneven problems (one graph launch) --------------------------
  *
  * Many correlations of different image and filter sizes run in ONE launch of
- * a persistent kernel, captured in a CUDA graph.  Problems are grouped into
+ * a CUDA graph, whose core is a persistent kernel.  Problems are grouped into
  * buckets (same filter size; image side below / at-or-above a split), each
  * bucket gets its own compile-time tile routine, and every block of the launch
  * takes (problem, tile) work items from a global counter until the list is
@@ -394,11 +394,13 @@ typedef struct {
 
 typedef struct ct_batch ct_batch;
 
-/* Plans a batch: validates every item (as ct_conv2d would), buckets the
- * problems, tunes (opts->tune) and compiles the persistent kernel, uploads the
- * problem table, the filters and the work list, and captures the launch (work
- * counter reset + kernel) in a CUDA graph.  Synchronous; device memory for the
- * tables is owned by the plan.  Up to 16 buckets per batch. */
+/* Plans a batch: validates every item (as ct_conv2d would), picks the solo
+ * problems (tuning their configuration per filter size, which runs kernels on
+ * the largest one's buffers), buckets the rest, tunes (opts->tune) and
+ * compiles the persistent kernel, uploads the problem table, tensor maps,
+ * filters and work list, and captures the solo launches plus the persistent
+ * launch (work counter reset + kernel) in a CUDA graph.  Synchronous; device
+ * memory for the tables is owned by the plan.  Up to 16 buckets per batch. */
 CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct_batch_opts* opts,
                                  ct_batch** out);
 /* Runs the planned batch once on `stream` (one graph launch; asynchronous).
@@ -407,7 +409,8 @@ CT_API ct_status ct_batch_run(ct_batch* b, void* stream);
 /* Reads the plan's error word (synchronously; call it after the runs have
  * completed): CT_OK, or CT_ERR_TIMEOUT when a block of an earlier run gave up
  * waiting for its input copies (its outputs are then incomplete).  The word is
- * sticky for the life of the plan. */
+ * sticky for the life of the plan.  A plan with solo launches also reports
+ * the device's error word (see ct_device_check; not cleared here). */
 CT_API ct_status ct_batch_check(const ct_batch* b);
 CT_API ct_status ct_batch_info_get(const ct_batch* b, ct_batch_info* out);
 /* Bucket k: its filter size, number of problems, tile configuration and the
