@@ -104,6 +104,18 @@ def aggregate_over_ranks(t_step_ms, flops_per_rank, device=None):
     return t_max, world * flops_per_rank / (t_max * 1e-3) / 1e9
 
 
+def from_rank0(obj):
+    """Rank 0's `obj` on every rank (a broadcast; the object itself in a
+    single process): replicas time the configuration rank 0 tuned instead of
+    each running the tuner, which would share the node's host cores."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return obj
+    buf = [obj if dist.get_rank() == 0 else None]
+    dist.broadcast_object_list(buf, src=0)
+    return buf[0]
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -302,8 +314,11 @@ def run_ours(args):
 
     rank, world, local = dist_env()
     if world > 1:
+        import datetime
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        # the other ranks wait in a broadcast while rank 0 tunes (minutes)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
+                                timeout=datetime.timedelta(minutes=30))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
@@ -347,6 +362,10 @@ def run_ours(args):
     if args.config:
         best = ct.config(*[int(v) for v in args.config.split(",")])
         n_valid = ct.Space(space).count(p)[1]
+    elif rank != 0:
+        # the replicas time the configuration rank 0 tunes
+        best_t, n_valid, tuning, analysis = from_rank0(None)
+        best = ct.config(*best_t)
     else:
         strategies = [args.strategy] + [s for s in args.extra_strategies.split(",") if s and s != args.strategy]
         tab = None
@@ -378,6 +397,7 @@ def run_ours(args):
             best_mode.setdefault(f"smem{r['use_smem']}_unroll{r['unroll']}", _short(r))
         analysis["best_per_staging_unroll"] = best_mode
         analysis["n_spilling"] = sum(1 for r in tab.valid() if r["spill_bytes"] > 0)
+        from_rank0((best.as_tuple(), n_valid, tuning, analysis))
 
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(int(2 * max(info.l2_bytes, 64 << 20)), dtype=torch.uint8, device=dev)

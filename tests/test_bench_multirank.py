@@ -1,5 +1,6 @@
 """The N > 1 host logic of bench.py on CPU: two gloo ranks report different
-step times; both see the slowest one, and the value counts both ranks' work."""
+step times; both see the slowest one, and the value counts both ranks' work;
+the configuration rank 0 tuned reaches the other rank."""
 import os
 import socket
 
@@ -27,9 +28,10 @@ def _rank(rank, world, port, q):
     t_ms = 2.0 if rank == 0 else 3.0          # rank 1 is the slow one
     dist.barrier()
     t_max, value = bench.aggregate_over_ranks(t_ms, 6e9)
+    tuned = bench.from_rank0(((16, 16, 4, 2, 1, 1), 5576, {"brute": {"evals": 5576}}) if rank == 0 else None)
     dist.barrier()
     dist.destroy_process_group()
-    q.put((rank, t_max, value))
+    q.put((rank, t_max, value, tuned))
 
 
 def test_two_gloo_ranks_take_the_slowest_step():
@@ -42,13 +44,15 @@ def test_two_gloo_ranks_take_the_slowest_step():
     for p in procs:
         p.join(120)
         assert p.exitcode == 0
-    res = sorted(q.get(timeout=5) for _ in range(2))
-    for rank, t_max, value in res:
+    res = sorted((q.get(timeout=5) for _ in range(2)), key=lambda r: r[0])
+    for rank, t_max, value, tuned in res:
         assert t_max == 3.0
         assert value == pytest.approx(2 * 6e9 / 3e-3 / 1e9)
+        assert tuned == ((16, 16, 4, 2, 1, 1), 5576, {"brute": {"evals": 5576}})
 
 
 def test_single_process_needs_no_collective():
     import bench
     t, v = bench.aggregate_over_ranks(2.0, 4e9)
     assert t == 2.0 and v == pytest.approx(4e9 / 2e-3 / 1e9)
+    assert bench.from_rank0({"a": 1}) == {"a": 1}
