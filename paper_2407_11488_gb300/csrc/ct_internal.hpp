@@ -174,6 +174,8 @@ public:
     std::shared_future<VariantPtr> request(uint64_t key, Job job, bool urgent = false);
     void forget(const VariantKey& k);
     void forget(uint64_t key);
+    // true when the job for k has finished, or is not in the pool
+    bool ready(const VariantKey& k);
     const std::string& cache_dir() const { return cache_dir_; }
     size_t queued();
     size_t threads() const { return threads_.size(); }

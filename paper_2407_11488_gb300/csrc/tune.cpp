@@ -3,6 +3,7 @@
 #include "ct_internal.hpp"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -10,6 +11,7 @@
 #include <limits>
 #include <set>
 #include <sstream>
+#include <thread>
 
 namespace ct {
 
@@ -68,6 +70,13 @@ std::shared_future<VariantPtr> CompilePool::request(uint64_t key, Job job, bool 
 }
 
 void CompilePool::forget(const VariantKey& k) { forget(k.packed()); }
+
+bool CompilePool::ready(const VariantKey& k)
+{
+    std::lock_guard<std::mutex> g(mu_);
+    auto it = futures_.find(k.packed());
+    return it == futures_.end() || it->second.wait_for(std::chrono::seconds(0)) == std::future_status::ready;
+}
 
 size_t CompilePool::queued()
 {
@@ -136,6 +145,8 @@ public:
     virtual ~Evaluator() = default;
     virtual void prefetch(const Entry&, bool urgent = false) { (void)urgent; }
     virtual bool queue_short() const { return true; }
+    // true when eval(e) would not wait for a compile
+    virtual bool ready(const Entry&) { return true; }
     virtual Measure eval(const Entry& e) = 0;
     double compile_wait_ms = 0, compile_cpu_ms = 0, bench_ms = 0;
     bool abort = false;   // set after an unrecoverable device error
@@ -183,6 +194,7 @@ public:
     VariantKey key(const Entry& e) const { return VariantKey{e.cfg, p_.filter_w, p_.filter_h, p_.dtype}; }
     void prefetch(const Entry& e, bool urgent) override { pool_.request(key(e), urgent); }
     bool queue_short() const override { return pool_.queued() < 2 * pool_.threads(); }
+    bool ready(const Entry& e) override { return pool_.ready(key(e)); }
 
     Measure eval(const Entry& e) override
     {
@@ -445,6 +457,12 @@ public:
     const Entry& entry(int64_t idx) const { return valid_[pos_.at(idx)]; }
     bool visited(int64_t idx) const { return row_of_.count(idx) != 0; }
     size_t n_rows() const { return rows.size(); }
+    // true when evaluate(e) would not wait for a compile
+    bool ready(const Entry& e)
+    {
+        return visited(e.index) || resume_.count(VariantKey{e.cfg, p_.filter_w, p_.filter_h, p_.dtype}.packed()) ||
+               ev_.ready(e);
+    }
 
     void prefetch(const Entry& e, bool urgent = false)
     {
@@ -548,10 +566,13 @@ static std::vector<int64_t> neighbours(const Space& s, const Driver& d, const ct
 // objective normalised by the first measured time, temperature cooled
 // geometrically from 1 to 1e-3 over the evaluation budget, Metropolis
 // acceptance, restart from the best point after budget/10 fresh evaluations
-// without improvement, memoised measurements.  `chains` walkers advance in
-// lock step: each round proposes one candidate per walker, the candidates are
-// compiled together (urgent requests), then measured one after another, so a
-// round costs about one compile latency instead of one per walker.
+// without improvement, memoised measurements.  `chains` walkers each keep one
+// candidate in flight (compiled as an urgent request, with the unmeasured
+// neighbours of the walker's point and candidate compiled speculatively while
+// the queue is short); the next candidate measured is that of the first
+// walker, in round-robin order, whose compile has finished, so no walker
+// waits for another's slow compile.  Without compiles (replay) every
+// candidate is ready and the walkers take turns in order.
 static void run_anneal(Driver& d, const Space& s, const std::vector<Entry>& valid, int64_t budget, uint64_t seed,
                        int chains, const bool* stop)
 {
@@ -561,6 +582,7 @@ static void run_anneal(Driver& d, const Space& s, const std::vector<Entry>& vali
         const Entry* cur = nullptr;
         double f = std::numeric_limits<double>::infinity();
         int64_t idle = 0;
+        const Entry* cand = nullptr;
     };
     std::vector<Walker> w((size_t)chains);
     for (auto& x : w) x.cur = &valid[rng.below(valid.size())];
@@ -573,72 +595,96 @@ static void run_anneal(Driver& d, const Space& s, const std::vector<Entry>& vali
         if (!std::isfinite(f_first) && std::isfinite(x.f)) f_first = x.f;
         if (x.f < f_best) { best = x.cur; f_best = x.f; }
     }
+    // the next candidate of a walker: a random neighbour of its point, a
+    // random unvisited point when it is stuck, or (on a failing point) a jump
+    auto propose = [&](Walker& x) -> const Entry* {
+        if (!std::isfinite(x.f)) {
+            x.cur = &valid[rng.below(valid.size())];
+            return x.cur;
+        }
+        std::vector<int64_t> nb = neighbours(s, d, x.cur->cfg);
+        bool all_seen = true;
+        for (int64_t i : nb) all_seen = all_seen && d.visited(i);
+        if (nb.empty() || (all_seen && x.idle > 2 * (int64_t)nb.size())) {
+            std::vector<const Entry*> fresh;
+            for (const auto& e : valid)
+                if (!d.visited(e.index)) fresh.push_back(&e);
+            if (fresh.empty()) return nullptr;
+            x.idle = 0;
+            return fresh[rng.below(fresh.size())];
+        }
+        return &d.entry(nb[rng.below(nb.size())]);
+    };
+    auto launch = [&](Walker& x) {
+        x.cand = propose(x);
+        if (!x.cand) return;
+        d.prefetch(*x.cand, true);
+        if (d.queue_short()) {   // speculative, behind the urgent requests
+            for (int64_t i : neighbours(s, d, x.cur->cfg)) d.prefetch(d.entry(i), false);
+            for (int64_t i : neighbours(s, d, x.cand->cfg)) d.prefetch(d.entry(i), false);
+        }
+    };
+    for (auto& x : w) launch(x);
     const double T0 = 1.0, T1 = 1e-3;
     const int64_t stall_limit = std::max<int64_t>(1, budget / 10);
     int64_t stall = 0, steps = 0;
     const int64_t max_steps = 200 * budget + 1000;
-    std::vector<const Entry*> cand((size_t)chains);
+    size_t rr = 0;
     while ((int64_t)d.n_rows() < budget && steps < max_steps) {
         if (stop && *stop) return;
         ++steps;
-        for (size_t m = 0; m < w.size(); ++m) {
-            Walker& x = w[m];
-            if (!std::isfinite(x.f)) {   // a walker on a failing point jumps
-                x.cur = &valid[rng.below(valid.size())];
-                cand[m] = x.cur;
-                continue;
+        // the first walker (round-robin) whose candidate is ready to measure
+        size_t m = w.size();
+        for (int spins = 0; m == w.size(); ++spins) {
+            bool any = false;
+            for (size_t k = 0; k < w.size(); ++k) {
+                const size_t j = (rr + k) % w.size();
+                if (!w[j].cand) continue;
+                any = true;
+                if (d.ready(*w[j].cand)) {
+                    m = j;
+                    break;
+                }
             }
-            std::vector<int64_t> nb = neighbours(s, d, x.cur->cfg);
-            bool all_seen = true;
-            for (int64_t i : nb) all_seen = all_seen && d.visited(i);
-            if (nb.empty() || (all_seen && x.idle > 2 * (int64_t)nb.size())) {
-                std::vector<const Entry*> fresh;
-                for (const auto& e : valid)
-                    if (!d.visited(e.index)) fresh.push_back(&e);
-                if (fresh.empty()) return;
-                cand[m] = fresh[rng.below(fresh.size())];
-                x.idle = 0;
-            } else {
-                cand[m] = &d.entry(nb[rng.below(nb.size())]);
+            if (!any) return;   // every point is visited
+            if (m == w.size()) {
+                if (spins > 200000) {   // ~20 s without a finished compile: measure the next in turn
+                    for (size_t k = 0; k < w.size() && m == w.size(); ++k)
+                        if (w[(rr + k) % w.size()].cand) m = (rr + k) % w.size();
+                } else {
+                    std::this_thread::sleep_for(std::chrono::microseconds(100));
+                }
             }
         }
-        for (const Entry* c : cand) d.prefetch(*c, true);
-        // speculative, behind the urgent candidates: the unmeasured neighbours
-        // of every walker's point and candidate (the next proposals come from
-        // them), while the compile queue is short
-        for (size_t m = 0; m < w.size() && d.queue_short(); ++m) {
-            for (int64_t i : neighbours(s, d, w[m].cur->cfg)) d.prefetch(d.entry(i), false);
-            for (int64_t i : neighbours(s, d, cand[m]->cfg)) d.prefetch(d.entry(i), false);
-        }
-        for (size_t m = 0; m < w.size() && (int64_t)d.n_rows() < budget; ++m) {
-            Walker& x = w[m];
-            bool fresh_eval = false;
-            const double f_c = d.evaluate(*cand[m], &fresh_eval);
-            if (!std::isfinite(f_first) && std::isfinite(f_c)) f_first = f_c;
-            x.idle = fresh_eval ? 0 : x.idle + 1;
-            if (!std::isfinite(x.f)) {
-                x.cur = cand[m];
+        rr = (m + 1) % w.size();
+        Walker& x = w[m];
+        bool fresh_eval = false;
+        const double f_c = d.evaluate(*x.cand, &fresh_eval);
+        if (!std::isfinite(f_first) && std::isfinite(f_c)) f_first = f_c;
+        x.idle = fresh_eval ? 0 : x.idle + 1;
+        if (!std::isfinite(x.f)) {
+            x.cur = x.cand;
+            x.f = f_c;
+        } else if (std::isfinite(f_c)) {
+            const double T = T0 * std::pow(T1 / T0, std::min(1.0, (double)d.n_rows() / (double)budget));
+            const double delta = (f_c - x.f) / f_first;
+            if (delta < 0 || rng.uniform() < std::exp(-delta / T)) {
+                x.cur = x.cand;
                 x.f = f_c;
-            } else if (std::isfinite(f_c)) {
-                const double T = T0 * std::pow(T1 / T0, std::min(1.0, (double)d.n_rows() / (double)budget));
-                const double delta = (f_c - x.f) / f_first;
-                if (delta < 0 || rng.uniform() < std::exp(-delta / T)) {
-                    x.cur = cand[m];
-                    x.f = f_c;
-                }
-            }
-            if (f_c < f_best) {
-                best = cand[m];
-                f_best = f_c;
-                stall = 0;
-            } else if (fresh_eval && ++stall >= stall_limit) {
-                for (auto& y : w) {
-                    y.cur = best;
-                    y.f = f_best;
-                }
-                stall = 0;
             }
         }
+        if (f_c < f_best) {
+            best = x.cand;
+            f_best = f_c;
+            stall = 0;
+        } else if (fresh_eval && ++stall >= stall_limit) {
+            for (auto& y : w) {
+                y.cur = best;
+                y.f = f_best;
+            }
+            stall = 0;
+        }
+        launch(x);
     }
 }
 
