@@ -233,6 +233,21 @@ def test_annealing_within_five_percent(ctlib):
     assert float(np.median(ratios)) <= 1.05, ratios
 
 
+@pytest.mark.parametrize("chains", [1, 4, 16])
+def test_annealing_replay_is_deterministic(ctlib, chains):
+    """Without compiles every walker's candidate is ready at once, so the
+    walkers take turns in order: one seed gives one evaluation sequence, with
+    any number of walkers, and the walkers share the budget."""
+    p = ctlib.make_problem(4096, 4096, 17, 17)
+    times = landscape("full", 17, 17, 5)
+    runs = [ctlib.tune_replay(p, "full", "anneal", times, seed=7, max_evals=200, anneal_chains=chains)
+            for _ in range(2)]
+    seqs = [[r["index"] for r in sorted(t.rows, key=lambda r: r["eval_order"])] for t in runs]
+    assert seqs[0] == seqs[1] and len(seqs[0]) == 200
+    other = ctlib.tune_replay(p, "full", "anneal", times, seed=8, max_evals=200, anneal_chains=chains)
+    assert [r["index"] for r in sorted(other.rows, key=lambda r: r["eval_order"])] != seqs[0]
+
+
 def test_annealing_with_failures_and_budget(ctlib):
     p = ctlib.make_problem(256, 256, 5, 5)
     times = landscape("small", 5, 5, 4, fail_every=5)
