@@ -240,12 +240,19 @@ typedef struct {
     int32_t compile_threads;  /* 0: one per host core */
     int32_t graph_below_us;   /* kernels shorter than this are timed as a graph of
                                  back-to-back launches (0: 50 us; < 0: never) */
-    int32_t anneal_chains;    /* ANNEAL: walkers advanced in lock step, their
-                                 candidates compiled together (0: 1) */
+    int32_t anneal_chains;    /* ANNEAL: independent walkers (0: 1); each keeps one
+                                 candidate in flight, and the next measured is that
+                                 of the first walker, in round-robin order, whose
+                                 compile has finished.  On the GPU that order depends
+                                 on compile times, so a seeded annealing run is
+                                 reproducible only under ct_tune_replay (where every
+                                 candidate is ready at once) */
     int32_t reserved;
     const char* cache_dir;    /* cubin cache for this run (NULL: library setting) */
     const char* resume_path;  /* JSONL table: rows found there are not re-measured,
                                  new rows are appended (NULL: none) */
+    const char* trace_path;   /* ANNEAL: JSONL trace of every walker step, restart
+                                 and start point, appended (NULL: none) */
 } ct_tune_opts;
 
 /* One row of a timing table. */

@@ -73,7 +73,8 @@ class DeviceInfo(ctypes.Structure):
 class TuneOpts(ctypes.Structure):
     _fields_ = [("seed", u64), ("sample_fraction", dbl), ("max_evals", i32), ("repeats", i32),
                 ("warmup", i32), ("flush_l2", i32), ("compile_threads", i32), ("graph_below_us", i32),
-                ("anneal_chains", i32), ("reserved", i32), ("cache_dir", cp), ("resume_path", cp)]
+                ("anneal_chains", i32), ("reserved", i32), ("cache_dir", cp), ("resume_path", cp),
+                ("trace_path", cp)]
 
 
 class Row(ctypes.Structure):
@@ -483,10 +484,10 @@ def _collect(t, best, write_path=None, space=None, flops=0.0) -> Table:
 
 
 def _opts(seed=0, sample_fraction=0.0, max_evals=0, repeats=0, warmup=0, flush_l2=False, compile_threads=0,
-          graph_below_us=0, anneal_chains=0, cache_dir=None, resume_path=None):
+          graph_below_us=0, anneal_chains=0, cache_dir=None, resume_path=None, trace_path=None):
     return TuneOpts(seed, sample_fraction, max_evals, repeats, warmup, int(flush_l2), compile_threads,
                     graph_below_us, anneal_chains, 0, cache_dir.encode() if cache_dir else None,
-                    resume_path.encode() if resume_path else None)
+                    resume_path.encode() if resume_path else None, trace_path.encode() if trace_path else None)
 
 
 def tune(problem: Problem, space="small", strategy="brute", *, image=None, filt=None, out=None,

@@ -572,9 +572,13 @@ static std::vector<int64_t> neighbours(const Space& s, const Driver& d, const ct
 // the queue is short); the next candidate measured is that of the first
 // walker, in round-robin order, whose compile has finished, so no walker
 // waits for another's slow compile.  Without compiles (replay) every
-// candidate is ready and the walkers take turns in order.
+// candidate is ready and the walkers take turns in order.  A restart moves
+// every walker to the best point and replaces its candidate in flight by one
+// proposed from there (a candidate proposed from the old point is dropped
+// unmeasured).  `trace` (may be NULL) receives one JSON line per start point,
+// step and restart.
 static void run_anneal(Driver& d, const Space& s, const std::vector<Entry>& valid, int64_t budget, uint64_t seed,
-                       int chains, const bool* stop)
+                       int chains, const bool* stop, FILE* trace)
 {
     Rng rng(seed ^ 0xA5A5A5A5ull);
     chains = std::max(1, std::min<int>(chains, (int)std::max<int64_t>(1, budget / 8)));
@@ -583,21 +587,32 @@ static void run_anneal(Driver& d, const Space& s, const std::vector<Entry>& vali
         double f = std::numeric_limits<double>::infinity();
         int64_t idle = 0;
         const Entry* cand = nullptr;
+        const Entry* from = nullptr;   // the point cand was proposed from
+        bool jump = false;             // cand is a jump, not a neighbour of `from`
+        int64_t epoch = 0;             // restarts before cand was proposed
     };
+    int64_t epoch = 0;
     std::vector<Walker> w((size_t)chains);
     for (auto& x : w) x.cur = &valid[rng.below(valid.size())];
     for (auto& x : w) d.prefetch(*x.cur, true);
     double f_first = std::numeric_limits<double>::infinity();
     const Entry* best = w[0].cur;
     double f_best = std::numeric_limits<double>::infinity();
-    for (auto& x : w) {
+    for (size_t k = 0; k < w.size(); ++k) {
+        Walker& x = w[k];
         x.f = d.evaluate(*x.cur);
         if (!std::isfinite(f_first) && std::isfinite(x.f)) f_first = x.f;
         if (x.f < f_best) { best = x.cur; f_best = x.f; }
+        if (trace)
+            fprintf(trace, "{\"ev\":\"start\",\"walker\":%zu,\"point\":%lld,\"f\":%.17g}\n", k,
+                    (long long)x.cur->index, std::isfinite(x.f) ? x.f : -1.0);
     }
     // the next candidate of a walker: a random neighbour of its point, a
     // random unvisited point when it is stuck, or (on a failing point) a jump
     auto propose = [&](Walker& x) -> const Entry* {
+        x.from = x.cur;
+        x.jump = true;
+        x.epoch = epoch;
         if (!std::isfinite(x.f)) {
             x.cur = &valid[rng.below(valid.size())];
             return x.cur;
@@ -613,6 +628,7 @@ static void run_anneal(Driver& d, const Space& s, const std::vector<Entry>& vali
             x.idle = 0;
             return fresh[rng.below(fresh.size())];
         }
+        x.jump = false;
         return &d.entry(nb[rng.below(nb.size())]);
     };
     auto launch = [&](Walker& x) {
@@ -662,27 +678,48 @@ static void run_anneal(Driver& d, const Space& s, const std::vector<Entry>& vali
         const double f_c = d.evaluate(*x.cand, &fresh_eval);
         if (!std::isfinite(f_first) && std::isfinite(f_c)) f_first = f_c;
         x.idle = fresh_eval ? 0 : x.idle + 1;
+        bool accepted = false;
         if (!std::isfinite(x.f)) {
             x.cur = x.cand;
             x.f = f_c;
+            accepted = true;
         } else if (std::isfinite(f_c)) {
             const double T = T0 * std::pow(T1 / T0, std::min(1.0, (double)d.n_rows() / (double)budget));
             const double delta = (f_c - x.f) / f_first;
             if (delta < 0 || rng.uniform() < std::exp(-delta / T)) {
                 x.cur = x.cand;
                 x.f = f_c;
+                accepted = true;
             }
         }
+        if (trace)
+            fprintf(trace,
+                    "{\"ev\":\"step\",\"walker\":%zu,\"epoch\":%lld,\"from\":%lld,\"cand\":%lld,\"jump\":%d,"
+                    "\"fresh\":%d,\"accepted\":%d,\"f\":%.17g}\n",
+                    m, (long long)x.epoch, (long long)(x.from ? x.from->index : -1), (long long)x.cand->index,
+                    x.jump ? 1 : 0, fresh_eval ? 1 : 0, accepted ? 1 : 0, std::isfinite(f_c) ? f_c : -1.0);
+        bool restart = false;
         if (f_c < f_best) {
             best = x.cand;
             f_best = f_c;
             stall = 0;
         } else if (fresh_eval && ++stall >= stall_limit) {
+            restart = true;
+            stall = 0;
+        }
+        if (restart) {
+            ++epoch;
+            if (trace)
+                fprintf(trace, "{\"ev\":\"restart\",\"epoch\":%lld,\"best\":%lld,\"f\":%.17g}\n",
+                        (long long)epoch, (long long)best->index, f_best);
+            // every walker continues from the best point; candidates proposed
+            // from the old points are replaced
             for (auto& y : w) {
                 y.cur = best;
                 y.f = f_best;
+                y.idle = 0;
+                if (&y != &x) launch(y);
             }
-            stall = 0;
         }
         launch(x);
     }
@@ -714,7 +751,11 @@ static ct_status run_strategy(const ct_problem& p, const Space& s, ct_strategy s
     } else if (st == CT_RANDOM) {
         run_list(d, random_sample(valid, budget, o.seed), window, stop);
     } else if (st == CT_ANNEAL) {
-        run_anneal(d, s, valid, budget, o.seed, o.anneal_chains > 0 ? o.anneal_chains : 1, stop);
+        FILE* trace = (o.trace_path && *o.trace_path) ? fopen(o.trace_path, "a") : nullptr;
+        if (o.trace_path && *o.trace_path && !trace)
+            return fail(CT_ERR_INVALID_ARG, "cannot open the trace file %s", o.trace_path);
+        run_anneal(d, s, valid, budget, o.seed, o.anneal_chains > 0 ? o.anneal_chains : 1, stop, trace);
+        if (trace) fclose(trace);
     } else {
         return fail(CT_ERR_INVALID_ARG, "unknown strategy %d", (int)st);
     }

@@ -248,6 +248,43 @@ def test_annealing_replay_is_deterministic(ctlib, chains):
     assert [r["index"] for r in sorted(other.rows, key=lambda r: r["eval_order"])] != seqs[0]
 
 
+@pytest.mark.parametrize("chains", [1, 16])
+def test_annealing_restart_moves_every_walker_to_the_best(ctlib, tmp_path, chains):
+    """Sec. 3's annealing restarts from the best point found so far.  After
+    each restart every walker's next step starts from that point (a candidate
+    a walker proposed from its old point is dropped, not measured), so the
+    step's candidate is the best point's neighbour or a jump; steps never come
+    from an earlier restart epoch; and every non-jump candidate is a neighbour
+    of the point it was proposed from."""
+    import json
+    p = ctlib.make_problem(4096, 4096, 17, 17)
+    times = landscape("full", 17, 17, 9)
+    trace = tmp_path / "trace.jsonl"
+    ctlib.tune_replay(p, "full", "anneal", times, seed=3, anneal_chains=chains, trace_path=str(trace))
+    ev = [json.loads(line) for line in open(trace)]
+    restarts = [k for k, e in enumerate(ev) if e["ev"] == "restart"]
+    assert len(restarts) >= 2, "the landscape must force restarts"
+    cfg_of = dict(ospace.enumerate_space("full", 17, 17, valid_only=False))
+    for k in restarts:
+        # the restart point is the fastest point measured before it
+        measured = [e for e in ev[:k] if e["ev"] in ("start", "step") and e["f"] > 0]
+        f_min = min(e["f"] for e in measured)
+        assert ev[k]["f"] == f_min and times[ev[k]["best"]] == f_min
+        nxt = next((j for j in restarts if j > k), len(ev))
+        for w in range(chains):
+            first = next((e for e in ev[k + 1:nxt] if e["ev"] == "step" and e["walker"] == w), None)
+            if first is None:
+                continue
+            assert first["epoch"] == ev[k]["epoch"] and first["from"] == ev[k]["best"], (k, w, first)
+            if not first["jump"]:
+                assert cfg_of[first["cand"]] in ospace.neighbours("full", cfg_of[ev[k]["best"]])
+    epochs = [e["epoch"] for e in ev if e["ev"] == "step"]
+    assert epochs == sorted(epochs)
+    for e in ev:
+        if e["ev"] == "step" and not e["jump"]:
+            assert cfg_of[e["cand"]] in ospace.neighbours("full", cfg_of[e["from"]])
+
+
 def test_annealing_with_failures_and_budget(ctlib):
     p = ctlib.make_problem(256, 256, 5, 5)
     times = landscape("small", 5, 5, 4, fail_every=5)
