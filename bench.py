@@ -116,6 +116,31 @@ def from_rank0(obj):
     return buf[0]
 
 
+class Rank0Failed(RuntimeError):
+    """Raised on the other ranks when rank 0's part of run_on_rank0 failed."""
+
+
+def run_on_rank0(fn):
+    """fn() on rank 0, its result on every rank (single process: fn()).  If
+    fn raises on rank 0, rank 0 broadcasts an error sentinel before
+    re-raising, so the other ranks raise Rank0Failed at once instead of
+    waiting in the broadcast until the process group's timeout."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return fn()
+    if dist.get_rank() == 0:
+        try:
+            res = fn()
+        except BaseException as e:
+            from_rank0(("error", f"{type(e).__name__}: {e}"))
+            raise
+        return from_rank0(("ok", res))[1]
+    tag, val = from_rank0(None)
+    if tag == "error":
+        raise Rank0Failed(f"rank 0 failed: {val}")
+    return val
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -359,14 +384,10 @@ def run_ours(args):
     tuning = {}
     analysis = {}
     tab = None
-    if args.config:
-        best = ct.config(*[int(v) for v in args.config.split(",")])
-        n_valid = ct.Space(space).count(p)[1]
-    elif rank != 0:
-        # the replicas time the configuration rank 0 tunes
-        best_t, n_valid, tuning, analysis = from_rank0(None)
-        best = ct.config(*best_t)
-    else:
+    held = {}
+
+    def tune_on_rank0():
+        tuning = {}
         strategies = [args.strategy] + [s for s in args.extra_strategies.split(",") if s and s != args.strategy]
         tab = None
         for k, strat in enumerate(strategies):
@@ -397,7 +418,17 @@ def run_ours(args):
             best_mode.setdefault(f"smem{r['use_smem']}_unroll{r['unroll']}", _short(r))
         analysis["best_per_staging_unroll"] = best_mode
         analysis["n_spilling"] = sum(1 for r in tab.valid() if r["spill_bytes"] > 0)
-        from_rank0((best.as_tuple(), n_valid, tuning, analysis))
+        held["tab"] = tab
+        return best.as_tuple(), n_valid, tuning, analysis
+
+    if args.config:
+        best = ct.config(*[int(v) for v in args.config.split(",")])
+        n_valid = ct.Space(space).count(p)[1]
+    else:
+        # rank 0 tunes; the replicas time the configuration it broadcasts
+        best_t, n_valid, tuning, analysis = run_on_rank0(tune_on_rank0)
+        best = ct.config(*best_t)
+        tab = held.get("tab")
 
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(int(2 * max(info.l2_bytes, 64 << 20)), dtype=torch.uint8, device=dev)

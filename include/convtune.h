@@ -103,8 +103,11 @@ typedef struct {
 
 /* ---- library and device ---------------------------------------------- */
 
+/* Version string naming the target architecture (sm_103a).  Paper: no
+ * counterpart (library plumbing). */
 CT_API const char* ct_version(void);
-/* Thread-local message of the last failing call on this thread ("" if none). */
+/* Thread-local message of the last failing call on this thread ("" if none).
+ * Paper: no counterpart (error reporting of the C-ABI). */
 CT_API const char* ct_last_error(void);
 
 typedef struct {
@@ -116,30 +119,41 @@ typedef struct {
     int32_t reserved;
 } ct_device_info;
 
-/* Current device facts; CT_ERR_UNSUPPORTED when no CUDA device is usable. */
+/* Current device facts; CT_ERR_UNSUPPORTED when no CUDA device is usable.
+ * Paper: Table 2 describes each GPU by these facts (compute units, clock,
+ * from which the single-precision peak follows). */
 CT_API ct_status ct_device_query(ct_device_info* out);
 
 /* Directory for the on-disk cubin cache (NULL or "" disables it).  The
- * default is taken from the CONVTUNE_CACHE_DIR environment variable. */
+ * default is taken from the CONVTUNE_CACHE_DIR environment variable.  Paper:
+ * Sec. 3 (the runner compiles the kernel once per configuration; the cache
+ * keeps those compiles across runs). */
 CT_API ct_status ct_set_cache_dir(const char* dir);
 
-/* Drops every loaded variant (modules are unloaded on the current device). */
+/* Drops every loaded variant (modules are unloaded on the current device).
+ * Paper: Sec. 3 (compiled configurations held by the runner). */
 CT_API ct_status ct_clear_cache(void);
 
 /* ---- configurations and variants -------------------------------------- */
 
 /* The baseline configuration: one output per thread, 32 x 8 threads,
- * global-memory reads, rolled filter-row loop. */
+ * global-memory reads, rolled filter-row loop.  Paper: a point of Table 1's
+ * space for the 2D convolution kernel of Sec. 5; the paper names no default,
+ * so this is the reading used for the tuned-vs-default speedup. */
 CT_API ct_status ct_default_config(const ct_problem* p, ct_config* out);
 
 /* Checks that (p, c) is launchable: argument ranges, threads per block and
  * the shared-memory tile against smem_limit_bytes (<= 0: the current
  * device's opt-in limit, or 232448 when there is no device).  Returns
- * CT_ERR_INVALID_CONFIG or CT_ERR_INVALID_ARG with a message otherwise. */
+ * CT_ERR_INVALID_CONFIG or CT_ERR_INVALID_ARG with a message otherwise.
+ * Paper: Sec. 3 (restrictions the user's tuning script places on the
+ * Table 1 values). */
 CT_API ct_status ct_check_config(const ct_problem* p, const ct_config* c, int32_t smem_limit_bytes);
 
 /* Compiles (or finds in a cache) the variant for (p, c) without loading it.
- * Runs on a machine without a GPU: NVRTC targets sm_103a directly. */
+ * Runs on a machine without a GPU: NVRTC targets sm_103a directly.  Paper:
+ * Sec. 3 (the runner compiles the kernel source with the configuration's
+ * parameter values, including unroll factors, as compile-time constants). */
 CT_API ct_status ct_compile(const ct_problem* p, const ct_config* c, ct_variant_info* info);
 
 /* ---- the correlation ---------------------------------------------------- */
@@ -149,10 +163,14 @@ CT_API ct_status ct_compile(const ct_problem* p, const ct_config* c, ct_variant_
  * then stored nothing).  Synchronous: call it once the launches to check have
  * completed.  CT_OK, or CT_ERR_TIMEOUT (and the word is cleared when clear is
  * nonzero).  ct_tune checks the word after every configuration it times and
- * records such a configuration as failed with CT_ERR_TIMEOUT. */
+ * records such a configuration as failed with CT_ERR_TIMEOUT.  Paper: no
+ * counterpart (failure capture of the bounded device waits). */
 CT_API ct_status ct_device_check(int32_t clear);
 
 /* out = correlate(image, filter) with configuration c, enqueued on stream.
+ * Paper: Sec. 5 "Benchmark kernels" (the 2D convolution kernel), run at one
+ * point of Table 1's tunable parameters (block_size_x/y, tile_size_x/y,
+ * use_shmem) plus Sec. 3's loop unrolling.
  * d_image: in_h x in_pitch elements of p->dtype.  h_filter: filter_h x
  * filter_w row-major host array (float for CT_F32, raw bf16 bits uint16_t for
  * CT_BF16); it is copied into the launch before return.  d_out: out_h x
@@ -166,7 +184,8 @@ CT_API ct_status ct_device_check(int32_t clear);
 CT_API ct_status ct_conv2d(const ct_problem* p, const ct_config* c, const void* d_image,
                            const void* h_filter, float* d_out, void* stream);
 
-/* End-to-end form of ct_conv2d for host-resident data: copies h_image to
+/* End-to-end form of ct_conv2d for host-resident data (Paper: the Sec. 5
+ * kernel; the host copies have no counterpart): copies h_image to
  * d_image_ws, runs the correlation into d_out_ws and copies the result to
  * h_out, then synchronises `stream`.  The work is split into bands of output
  * rows (up to 8, at least 256 rows each) on library-owned streams so that the
@@ -178,13 +197,13 @@ CT_API ct_status ct_conv2d(const ct_problem* p, const ct_config* c, const void* 
 CT_API ct_status ct_conv2d_host(const ct_problem* p, const ct_config* c, const void* h_image,
                                 const void* h_filter, float* h_out, void* d_image_ws,
                                 float* d_out_ws, void* stream);
-/* ct_conv2d_host with host rows of their own pitch (elements, >= the row
+/* (Paper: as ct_conv2d_host.)  ct_conv2d_host with host rows of their own pitch (elements, >= the row
  * width; no alignment needed): only the valid columns are copied, with 2D
  * copies, into the workspaces laid out by p's pitches. */
 CT_API ct_status ct_conv2d_host_pitched(const ct_problem* p, const ct_config* c, const void* h_image,
                                         int64_t h_in_pitch, const void* h_filter, float* h_out,
                                         int64_t h_out_pitch, void* d_image_ws, float* d_out_ws, void* stream);
-/* Asynchronous form of ct_conv2d_host_pitched: the work starts after what is
+/* (Paper: as ct_conv2d_host.)  Asynchronous form of ct_conv2d_host_pitched: the work starts after what is
  * queued on `stream`, the call returns once it is enqueued, and completion
  * (output in h_out) is recorded on the caller's CUDA event done_event
  * (cudaEvent_t); `stream` is not made to wait.  Consecutive calls therefore
@@ -210,19 +229,25 @@ typedef struct ct_space ct_space;
  *   "paper": Table 1's convolution values: block_x 16k (k = 1..16) x
  *            block_y {1,2,4,8,16} x tile {1..4}^2 x smem {0,1} x unroll {0,1}
  * Restrictions (applied per problem): threads per block <= 1024 and the
- * shared-memory tile within the device limit. */
+ * shared-memory tile within the device limit.  Paper: Sec. 3 (the tunable
+ * parameters and their values, given by the user's tuning script), Table 1
+ * (the 2D convolution kernel's parameters and values). */
 CT_API ct_status ct_space_builtin(const char* name, ct_space** out);
 /* A space from JSON: {"block_x":[...], "block_y":[...], "tile_x":[...],
  * "tile_y":[...], "use_smem":[...], "unroll":[...]} (missing keys take the
- * single value of the default configuration). */
+ * single value of the default configuration).  Paper: Sec. 3 (the user's
+ * dictionary of tunable parameters and values), Table 1. */
 CT_API ct_status ct_space_from_json(const char* json, ct_space** out);
+/* Releases a space.  Paper: as ct_space_builtin. */
 CT_API void ct_space_free(ct_space* s);
 /* Number of raw points and of points valid for p (smem_limit as in
- * ct_check_config). */
+ * ct_check_config).  Paper: Sec. 3 and Sec. 6 (size of each kernel's search
+ * space after its restrictions; 4,362 points for the convolution). */
 CT_API ct_status ct_space_count(const ct_space* s, const ct_problem* p, int32_t smem_limit_bytes,
                                 int64_t* n_raw, int64_t* n_valid);
 /* Writes up to cap valid configurations for p, in canonical order, with their
- * canonical indices (either output may be NULL); *n gets the total. */
+ * canonical indices (either output may be NULL); *n gets the total.  Paper:
+ * Sec. 3 (the configurations the strategies draw from), Table 1 order. */
 CT_API ct_status ct_space_enumerate(const ct_space* s, const ct_problem* p, int32_t smem_limit_bytes,
                                     ct_config* cfgs, int64_t* indices, int64_t cap, int64_t* n);
 
@@ -289,7 +314,10 @@ typedef struct ct_table ct_table;
  * buffers filled from opts->seed and frees them before return; h_filter may
  * be NULL (seeded filter).  Synchronous.  *best_out gets the fastest config
  * (ties: lower canonical index); *table_out a library-owned table (free with
- * ct_table_free). */
+ * ct_table_free).  Paper: Sec. 3 (the strategies layer chooses the
+ * configurations to try; the runners compile, launch and time each one with
+ * events recorded before and after the kernel, and every configuration's
+ * result is returned). */
 CT_API ct_status ct_tune(const ct_problem* p, const ct_space* s, ct_strategy st,
                          const ct_tune_opts* opts, const void* d_image, const void* h_filter,
                          float* d_out, ct_config* best_out, ct_table** table_out);
@@ -297,15 +325,20 @@ CT_API ct_status ct_tune(const ct_problem* p, const ct_space* s, ct_strategy st,
 /* The same strategies driven by a given timing landscape instead of the GPU:
  * the "measurement" of the configuration with canonical index k is
  * times_ms[k] (k < n_times; NaN or <= 0 marks a failing configuration).
- * Needs no device.  Used to study and test strategies offline. */
+ * Needs no device.  Used to study and test strategies offline.  Paper: Sec. 3
+ * (the strategies layer, here driven by a recorded landscape). */
 CT_API ct_status ct_tune_replay(const ct_problem* p, const ct_space* s, ct_strategy st,
                                 const ct_tune_opts* opts, const double* times_ms, int64_t n_times,
                                 ct_config* best_out, ct_table** table_out);
 
+/* Access to a timing table: its row count, row i (0-based, in evaluation
+ * order), the run's summary, a JSON-lines copy (one object per row; the
+ * format ct_tune_opts.resume_path reads back), and its release.  Paper: Sec. 3
+ * (the result of every configuration tried is returned to the user), Table 5
+ * (the best configurations listed with their parameter values). */
 CT_API int64_t ct_table_size(const ct_table* t);
 CT_API ct_status ct_table_row(const ct_table* t, int64_t i, ct_row* out);
 CT_API ct_status ct_table_info_get(const ct_table* t, ct_table_info* out);
-/* Writes the table as JSON lines (one object per row). */
 CT_API ct_status ct_table_write(const ct_table* t, const char* path);
 CT_API void ct_table_free(ct_table* t);
 
@@ -358,7 +391,12 @@ CT_API ct_status ct_table_analyze(const ct_table* t, const ct_space* s, double f
  * tile); a tile's halo box is at most 256 x 256 elements, and a problem spans
  * at most 65535 tiles along each side (otherwise CT_ERR_UNSUPPORTED).  A block
  * that waits more than about two seconds for its copies gives up, records the
- * failure in the plan's error word and exits; ct_batch_check reports it. */
+ * failure in the plan's error word and exits; ct_batch_check reports it.
+ *
+ * Paper: batching has no counterpart in the paper (it tunes one problem at a
+ * time, Sec. 3); the per-bucket choice of tile uses its performance
+ * portability, Eq. 2, over the application efficiencies of Eq. 3, with the
+ * bucket's problem shapes in the role of the platforms. */
 
 typedef struct {
     const void* d_image;   /* in_h x in_pitch elements of the batch dtype (caller-owned, kept alive) */
@@ -407,27 +445,34 @@ typedef struct ct_batch ct_batch;
  * compiles the persistent kernel, uploads the problem table, tensor maps,
  * filters and work list, and captures the solo launches plus the persistent
  * launch (work counter reset + kernel) in a CUDA graph.  Synchronous; device
- * memory for the tables is owned by the plan.  Up to 16 buckets per batch. */
+ * memory for the tables is owned by the plan.  Up to 16 buckets per batch.
+ * Paper: Eqs. 2-3 (bucket tiles), Sec. 3 (per-size tuning of the solo
+ * launches); the batch itself has no counterpart. */
 CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct_batch_opts* opts,
                                  ct_batch** out);
 /* Runs the planned batch once on `stream` (one graph launch; asynchronous).
- * Runs of one plan must not overlap: they share its work counter. */
+ * Runs of one plan must not overlap: they share its work counter.  Paper: no
+ * counterpart (each problem's arithmetic is the Sec. 5 kernel's). */
 CT_API ct_status ct_batch_run(ct_batch* b, void* stream);
 /* Reads the plan's error word (synchronously; call it after the runs have
  * completed): CT_OK, or CT_ERR_TIMEOUT when a block of an earlier run gave up
  * waiting for its input copies (its outputs are then incomplete).  The word is
  * sticky for the life of the plan.  A plan with solo launches also reports
- * the device's error word (see ct_device_check; not cleared here). */
+ * the device's error word (see ct_device_check; not cleared here).  Paper:
+ * no counterpart (failure capture). */
 CT_API ct_status ct_batch_check(const ct_batch* b);
+/* The plan's shape, timings and persistent-launch resources.  Paper: no
+ * counterpart. */
 CT_API ct_status ct_batch_info_get(const ct_batch* b, ct_batch_info* out);
 /* Bucket k: its filter size, number of problems, tile configuration and the
  * PP score (Eq. 2) of that configuration over the bucket's measured shapes
- * (NaN when the bucket was not tuned). */
+ * (NaN when the bucket was not tuned).  Paper: Eq. 2 (PP), Eq. 3. */
 CT_API ct_status ct_batch_bucket(const ct_batch* b, int32_t k, int32_t* filter_w, int32_t* filter_h,
                                  int32_t* n_items, ct_bucket_config* cfg, double* pp);
 /* Bucket index of item i (in the order given to ct_batch_create); -1 for a
- * problem that runs as its own launch. */
+ * problem that runs as its own launch.  Paper: no counterpart. */
 CT_API int32_t ct_batch_item_bucket(const ct_batch* b, int32_t i);
+/* Releases the plan, its graph and its device tables.  Paper: no counterpart. */
 CT_API void ct_batch_free(ct_batch* b);
 
 /* ---- serving: continuous batching under a device-memory budget ------------
@@ -445,7 +490,11 @@ CT_API void ct_batch_free(ct_batch* b);
  * (same parity as filter_min) has one resident tile configuration, tuned at
  * creation when opts->tune is set, so a result does not depend on which
  * requests shared its launch.  All waits are host-side and bounded by the
- * caller's timeout; no device code waits. */
+ * caller's timeout; no device code waits.
+ *
+ * Paper: serving has no counterpart in the paper; the resident per-size tile
+ * configurations are tuned as in Sec. 3, and each request's arithmetic is the
+ * Sec. 5 kernel's.  Every ct_server_* call below falls under this note. */
 
 typedef struct {
     int64_t mem_budget_bytes; /* device memory for images, outputs and launch tables */
@@ -519,15 +568,16 @@ CT_API void ct_server_destroy(ct_server* s);
  * but with a kernel compiled ahead of time and all per-call scratch (work
  * counter, problem table, tile prefix sums, FP32 filters) in one statically
  * allocated 1 MiB device array: it calls no cudaMalloc, cudaFree or other
- * allocating routine.  Every GPU that loads the library holds that array until
+ * allocating routine.  Its outputs are bit-identical to ct_conv2d's.  Every GPU that loads the library holds that array until
  * the process exits.
  *
  * items / n / dtype as for ct_batch_create (n <= 1024; the problem table, the
  * prefix sums and every filter must fit the 1 MiB scratch, otherwise
- * CT_ERR_INVALID_ARG with the needed size).  Enqueued on `stream`; the copy of
- * the tables from host memory makes the call wait for work already queued on
- * that stream.  The first call on a device looks up the scratch array's device
- * address (make that first call before any stream capture).  All calls share
+ * CT_ERR_INVALID_ARG with the needed size).  Enqueued on `stream`: one
+ * host-to-device copy of the tables (from a library-owned host staging area,
+ * filled under a lock) followed by one kernel launch.  The first call on a
+ * device looks up the scratch array's device address (make that first call
+ * before any stream capture).  All calls share
  * the one array and each overwrites it (the work counter is reset by every
  * call): calls whose work overlaps on the GPU race, so serialise them (one
  * stream, or wait for the previous call). */

@@ -51,8 +51,53 @@ def test_two_gloo_ranks_take_the_slowest_step():
         assert tuned == ((16, 16, 4, 2, 1, 1), 5576, {"brute": {"evals": 5576}})
 
 
+def _rank_fail(rank, world, port, q):
+    import sys
+    import time
+    import torch.distributed as dist
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import datetime
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(minutes=10))
+    import bench
+
+    def tune():
+        raise ValueError("no configuration compiled")
+    t0 = time.time()
+    try:
+        bench.run_on_rank0(tune)
+        outcome = "returned"
+    except bench.Rank0Failed as e:
+        outcome = "Rank0Failed: " + str(e)
+    except ValueError as e:
+        outcome = "ValueError: " + str(e)
+    q.put((rank, outcome, time.time() - t0))
+    dist.destroy_process_group()
+
+
+def test_rank0_failure_reaches_the_other_rank_at_once():
+    """Rank 0's tuning raises: rank 0 re-raises its own error, rank 1 raises
+    Rank0Failed with rank 0's message within seconds, not at the process
+    group's timeout (10 minutes here)."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_fail, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = dict((r, (o, t)) for r, o, t in (q.get(timeout=5) for _ in range(2)))
+    assert res[0][0] == "ValueError: no configuration compiled"
+    assert res[1][0].startswith("Rank0Failed") and "no configuration compiled" in res[1][0]
+    assert res[1][1] < 60.0
+
+
 def test_single_process_needs_no_collective():
     import bench
     t, v = bench.aggregate_over_ranks(2.0, 4e9)
     assert t == 2.0 and v == pytest.approx(4e9 / 2e-3 / 1e9)
     assert bench.from_rank0({"a": 1}) == {"a": 1}
+    assert bench.run_on_rank0(lambda: 5) == 5
