@@ -215,20 +215,36 @@ def cpu_rate_sample(img, f, out_w, rows):
     return time.perf_counter() - t
 
 
-def cpu_baseline(img, f, out_w, out_h, seconds):
+def parity_record(gpu, ref, S, what):
+    """Per-pixel check |gpu - ref| <= 1e-5 * S (the FP32 parity bound)."""
+    import numpy as np
+    err = np.abs(gpu.astype(np.float64) - ref)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rel = np.where(S > 0, err / S, np.where(err == 0, 0.0, np.inf))
+    return {"n": int(ref.size), "max_err_over_S": float(np.max(rel)) if rel.size else 0.0,
+            "bound": 1e-5, "ok": bool(np.all(err <= 1e-5 * S)), "over": what}
+
+
+def cpu_baseline(img, f, out_w, out_h, seconds, gpu_out=None):
     """The oracle, as it stands, on all host cores over a bounded sample of
     the workload: bands of output rows, repeated until `seconds` of CPU
-    work; value in GFLOP/s (2 flops per tap)."""
+    work; value in GFLOP/s (2 flops per tap).  With `gpu_out` (the GPU's
+    result of the same workload, host array (out_h, >= out_w)), the oracle's
+    first band is also compared with it pixel by pixel ("parity")."""
     import oracle
     fh, fw = f.shape
     dt0 = cpu_rate_sample(img, f, out_w, 16)
     rows = int(max(16, min(out_h, 16 * (seconds / 4) / max(dt0, 1e-6))))
     done_rows, t_total, reps = 0, 0.0, 0
+    parity = None
     while t_total < seconds and reps < 100:
         y0 = (reps * rows) % max(1, out_h - rows + 1)
         t = time.perf_counter()
-        oracle.corr2d_f64(img[y0:y0 + rows + fh - 1], f, out_w, rows)
+        ref, S = oracle.corr2d_f64(img[y0:y0 + rows + fh - 1], f, out_w, rows)
         t_total += time.perf_counter() - t
+        if gpu_out is not None and parity is None:
+            parity = parity_record(gpu_out[y0:y0 + rows, :out_w], ref, S,
+                                   f"output rows {y0}..{y0 + rows - 1}, all {out_w} columns")
         done_rows += rows
         reps += 1
     flops = 2.0 * done_rows * out_w * fw * fh
@@ -242,7 +258,8 @@ def cpu_baseline(img, f, out_w, out_h, seconds):
             "sample": f"{reps} bands of {rows} output rows x {out_w} cols (filter {fw}x{fh}) of the "
                       f"{out_w}x{out_h} workload, {t_total:.1f} s of FP64 CPU work",
             "value_1thread": 2.0 * rows1 * out_w * fw * fh / t1 / 1e9,
-            "sample_1thread": f"{rows1} output rows x {out_w} cols, {t1:.1f} s", "cpu_model": cpu_model()}
+            "sample_1thread": f"{rows1} output rows x {out_w} cols, {t1:.1f} s", "cpu_model": cpu_model(),
+            "parity": parity}
 
 
 def cpu_model():
@@ -462,6 +479,7 @@ def run_ours(args):
     clocks.mark("timed_start")
     ms, tw0, tw1 = timed_loop(best, args.steps, max(3, args.warmup))
     clocks.mark("timed_end")
+    gpu_out = d_out[:, :ow].cpu().numpy() if rank == 0 else None   # the timed configuration's result
     default = ct.default_config()
     ms_def, _, _ = timed_loop(default, max(50, args.steps // 10), 5)
     t_step, value = aggregate_over_ranks(sum(ms) / len(ms), flops, dev)
@@ -544,6 +562,8 @@ def run_ours(args):
                    "strategy": "fixed --config" if args.config else args.strategy,
                    "tuned_config": best.as_dict(),
                    "l2": "flushed (2x L2 write) between timed iterations", "parallelism": f"replicas x{world}"},
+        "step_ms": {"mean": statistics.mean(ms), "median": statistics.median(ms), "min": min(ms),
+                    "max": max(ms), "n": len(ms), "value_from": "mean (max over ranks)"},
         "pct_fp32_peak": 100.0 * achieved / fp32_peak,
         "tuned_vs_default": statistics.median(ms_def) / statistics.median(ms),
         "default_ms": statistics.median(ms_def),
@@ -565,7 +585,9 @@ def run_ours(args):
         import oracle
         oracle.build()
         f_np = f.float().numpy() if hasattr(f, "float") else f
-        line["cpu_baseline"] = cpu_baseline(img, f_np, ow, oh, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(img, f_np, ow, oh, args.cpu_seconds, gpu_out=gpu_out)
+        line["parity"] = dict(line["cpu_baseline"].pop("parity") or {}, config=best.as_dict(),
+                              against="FP64 oracle (the cpu_baseline leg's first band)")
         if tab is not None:
             # the oracle's exhaustive CPU-side ranking of the same timing table
             from oracle import analysis as oan

@@ -1,0 +1,111 @@
+"""Every configuration of the full tuning space against the FP64 oracle.
+
+The tuner compiles and times every point of the space (Sec. 3; Table 1's
+parameters plus the unroll switch), so every point must compute the same
+correlation.  The problems are ragged (no side a multiple of any tile), the
+image's padding columns and the rows below it hold NaN (a read outside the
+valid input shows up as NaN in an output), and the output sits inside NaN
+sentinel guard bands (a store outside it is caught).  Per pixel
+|gpu - oracle| <= 1e-5 * sum|in*f|, and all configurations of one problem are
+bit-identical (each adds the taps of an output in (i, j) order with one FMA
+each).  Compiles go through the library's on-disk cubin cache in the
+benchmark's default location, so a benchmark run after these tests finds the
+17x17 variants already built."""
+import concurrent.futures as cf
+import os
+import tempfile
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+from oracle import space as ospace
+from tests.gpu_util import assert_parity, run_config
+
+pytestmark = pytest.mark.gpu
+
+NAN_ROWS = 8
+
+
+def _cfg(ct, d):
+    return ct.config(d["block_x"], d["block_y"], d["tile_x"], d["tile_y"], d["smem"], d["unroll"])
+
+
+def _image_with_nan_rows(img, device, bf16):
+    """The image on the device followed by NAN_ROWS rows of NaN; returns the
+    (in_h, pitch) view, whose allocation continues with the NaN rows."""
+    full = np.full((img.shape[0] + NAN_ROWS, img.shape[1]), np.nan, dtype=np.float32)
+    full[:img.shape[0]] = img
+    t = torch.from_numpy(full)
+    if bf16:
+        t = t.to(torch.bfloat16)
+    return t.to(device)[:img.shape[0]]
+
+
+def _sweep(ct, device, ow, oh, fw, fh, seed, every, bf16=False):
+    img, f = synthetic.make_problem(seed, ow, oh, fw, fh, pad_value=np.nan, extra_pitch=8 if bf16 else 4,
+                                    pitch_align=8 if bf16 else 4)
+    if bf16:
+        img_bits = torch.from_numpy(img).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        f_t = torch.from_numpy(np.ascontiguousarray(f)).to(torch.bfloat16)
+        f_bits = f_t.view(torch.int16).numpy().view(np.uint16)
+        ref, S = oracle.corr2d_bf16_f64(img_bits, f_bits, ow, oh)
+        filt = f_t
+    else:
+        ref, S = oracle.corr2d_f64(img, f, ow, oh)
+        filt = f
+    d_img = _image_with_nan_rows(img, device, bf16)
+    in_w = ow + fw - 1
+    p = ct.problem_for(d_img, filt, in_w=in_w)
+    ents = ospace.enumerate_space("full", fw, fh)[::every]
+    cfgs = [_cfg(ct, c) for _, c in ents]
+    lib_cfgs = {c.as_tuple() for _, c in ct.Space("full").enumerate(p)}
+    assert {c.as_tuple() for c in cfgs} <= lib_cfgs
+
+    cache = os.path.join(tempfile.gettempdir(), f"convtune-cache-{os.getuid()}")
+    ct.set_cache_dir(cache)
+    try:
+        first = None
+        chunk = 256
+        with cf.ThreadPoolExecutor(os.cpu_count() or 8) as ex:
+            nxt = ex.map(lambda c: ct.compile_variant(p, c), cfgs[:chunk])
+            for k in range(0, len(cfgs), chunk):
+                list(nxt)                                  # this chunk is compiled
+                if k + chunk < len(cfgs):                  # the next one compiles while this one runs
+                    nxt = ex.map(lambda c: ct.compile_variant(p, c), cfgs[k + chunk:k + 2 * chunk])
+                for c in cfgs[k:k + chunk]:
+                    out, ok = run_config(ct, d_img, filt, c, ow, oh, in_w=in_w)
+                    assert ok, f"guard band overwritten by {c}"
+                    assert_parity(out, ref, S, f"{ow}x{oh}/{fw}x{fh} {c}")
+                    if first is None:
+                        first = out
+                    else:
+                        assert np.array_equal(out.view(np.uint32), first.view(np.uint32)), f"{c} differs bitwise"
+                ct.clear_cache()                           # unload this chunk's modules
+        ct.device_check()
+    finally:
+        ct.set_cache_dir(None)
+    return len(cfgs)
+
+
+def test_full_space_every_config_17x17(ctlib, cuda_device):
+    """All 5,576 valid points of the full space for a 17x17 filter (the
+    filter of the 4096x4096 workload) on a 333x157 output."""
+    n = _sweep(ctlib, cuda_device, 333, 157, 17, 17, seed=21, every=1)
+    assert n == 5576
+
+
+def test_full_space_eighth_5x7(ctlib, cuda_device):
+    """Every 8th valid point (canonical order) for a 5-wide, 7-high filter on
+    a 301x163 output."""
+    n = _sweep(ctlib, cuda_device, 301, 163, 5, 7, seed=22, every=8)
+    assert n == len(ospace.enumerate_space("full", 5, 7)[::8])
+
+
+def test_full_space_bf16_sixteenth_9x9(ctlib, cuda_device):
+    """BF16 storage: every 16th valid point for the 9x9 filter of the BF16
+    workloads on a 259x131 output, against the oracle on the BF16 values."""
+    n = _sweep(ctlib, cuda_device, 259, 131, 9, 9, seed=23, every=16, bf16=True)
+    assert n == len(ospace.enumerate_space("full", 9, 9)[::16])
