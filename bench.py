@@ -85,6 +85,10 @@ def parse():
     ap.add_argument("--cold-cache", action="store_true",
                     help="give every strategy its own empty cubin cache (cold compile timings)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="full workload: skip the batched and BF16 sub-records measured after the headline")
+    ap.add_argument("--bf16-evals", type=int, default=0,
+                    help="annealing budget of each BF16 tuning run (0: 10 %% of the space)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -355,30 +359,10 @@ def run_ours(args):
     import torch
 
     rank, world, local = dist_env()
-    if world > 1:
-        import datetime
-        import torch.distributed as dist
-        # the other ranks wait in a broadcast while rank 0 tunes (minutes)
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
-                                timeout=datetime.timedelta(minutes=30))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
-    from paper_2407_11488_gb300 import build as _build
-    if local == 0:
-        _build.build()
-    if world > 1:
-        torch.distributed.barrier()
-    import paper_2407_11488_gb300 as ct
+    ct, dev, info, pk, fp32_peak, sm_max_mhz = setup(args)
     import synthetic
 
-    cache_dir = args.cache_dir or os.path.join(tempfile.gettempdir(), f"convtune-cache-{os.getuid()}")
-    ct.set_cache_dir(cache_dir)
-    info = ct.device_query()
-    pk = peaks()
-    sm_max_mhz = float(pk.get("sm_max_mhz") or (info.clock_max_khz / 1e3) or 2070.0)
-    fp32_peak = info.sm_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12   # TFLOP/s
-
+    extras = {}
     ow, oh, fs, seed, space, storage = WORKLOADS[args.workload]
     bf16 = storage == "bf16"
     img, f = synthetic.make_problem(seed, ow, oh, fs, fs, pitch_align=8 if bf16 else 4)
@@ -581,6 +565,33 @@ def run_ours(args):
         "clocks": clk,
         "device": info.name.decode(),
     }
+    if rank == 0 and args.workload == "full" and not args.no_extras:
+        # measured after the headline, outside its timed region: the batched
+        # workload (the metric's batched p99 latency) and the BF16 storage cases
+        ct.clear_cache()
+        bm = measure_batch(args, ct, dev, info, pk, fp32_peak, 1, plain_cfg={fs: best})
+        extras["batched"] = {
+            "workload": batch_workload_name(), "total_gflop": bm["flops"] / 1e9, "steps": bm["k"],
+            "p50_ms": bm["p50"], "p99_ms": bm["p99"], "mean_ms": bm["t_b"],
+            "gflops": bm["flops"] / (bm["t_b"] * 1e-3) / 1e9, "plain_ms": bm["t_p"],
+            "plain_graph_ms": bm["t_pg"], "persistent_only_ms": bm["t_persist"],
+            "batched_vs_plain": bm["t_p"] / bm["t_b"], "batched_vs_plain_graph": bm["t_pg"] / bm["t_b"],
+            "bit_identical_to_plain": bm["identical"], "composite_bound_ms": bm["peak_s"] * 1e3,
+            "frac_of_bound": bm["peak_s"] * 1e3 / bm["t_b"], "n_solo": bm["binfo"]["n_solo"],
+            "n_buckets": bm["binfo"]["n_buckets"], "plan_s": bm["plan_s"], "plain_tune_s": bm["plain_tune_s"],
+            "e2e_gflops": bm["flops"] / bm["te"] / 1e9, "clocks": bm["clocks"]}
+        line["batched_p50_ms"] = bm["p50"]
+        line["batched_p99_ms"] = bm["p99"]
+        line["batched_vs_plain"] = bm["t_p"] / bm["t_b"]
+        line["bit_identical_to_plain"] = bm["identical"]
+        extras["batch_results"] = bm.pop("results")
+        del bm
+        ct.clear_cache()
+        extras["bf16"] = []
+        for case in BF16_CASES:
+            rec, data = measure_bf16(args, ct, dev, info, fp32_peak, case)
+            extras["bf16"].append((rec, data))
+        torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -598,6 +609,17 @@ def run_ours(args):
                 "rows": len(rows), "ms": (time.perf_counter() - t) * 1e3,
                 "same_optimum_as_the_tuner": ost is not None and
                 ost["best_index"] == tab.rows[tab.info["best_row"]]["index"]}
+    if rank == 0 and "batched" in extras:
+        line["batched"] = extras["batched"]
+        if not args.no_cpu_baseline:
+            cb = cpu_baseline_batch(extras["batch_results"], args.cpu_seconds / 2)
+            line["batched"]["parity"] = cb.pop("parity")
+            line["batched"]["cpu_baseline"] = cb
+        line["bf16"] = []
+        for rec, data in extras["bf16"]:
+            if not args.no_cpu_baseline:
+                rec["errors"] = cpu_baseline_bf16(data)
+            line["bf16"].append(rec)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -606,36 +628,19 @@ def run_ours(args):
     return 0
 
 
-def run_batch(args):
+def measure_batch(args, ct, dev, info, pk, fp32_peak, world, plain_cfg=None):
     """64 uneven correlations: the plain per-problem path (one ct_conv2d per
     problem with the configuration tuned for its filter size; also timed as
     one captured CUDA graph, which leaves out the host's per-launch cost)
     against one graph launch of the batch plan (problems that fill the GPU
     alone as their own launches, the rest in one persistent launch; also
     timed with every problem in the persistent launch), same inputs and
-    outputs."""
+    outputs.  plain_cfg: {filter size: Config} already tuned (those sizes
+    are not tuned again).  Returns a dict of measurements and the problems."""
     import numpy as np
     import torch
-
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    from paper_2407_11488_gb300 import build as _build
-    if local == 0:
-        _build.build()
-    if world > 1:
-        torch.distributed.barrier()
-    import paper_2407_11488_gb300 as ct
     import synthetic
 
-    ct.set_cache_dir(args.cache_dir or os.path.join(tempfile.gettempdir(), f"convtune-cache-{os.getuid()}"))
-    info = ct.device_query()
-    pk = peaks()
-    sm_max_mhz = float(pk.get("sm_max_mhz") or (info.clock_max_khz / 1e3) or 2070.0)
-    fp32_peak = info.sm_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     shapes = synthetic.uneven_batch(BATCH["seed"], BATCH["count"], BATCH["side_lo"], BATCH["side_hi"],
                                     BATCH["filters"])
     keep = [k for k, (_, fs) in enumerate(shapes) if not args.batch_filter or fs == args.batch_filter]
@@ -654,9 +659,12 @@ def run_batch(args):
 
     # plain path: tune once per filter size on that size's largest problem
     t0 = time.time()
-    cfg_for = {}
+    cfg_for = dict(plain_cfg or {})
     tuning = {}
     for fs in sorted(set(fs for _, fs in shapes)) if args.batch_plain == "tune" else []:
+        if fs in cfg_for:
+            tuning[f"plain_f{fs}"] = {"best": cfg_for[fs].as_dict(), "from": "the headline tuning"}
+            continue
         big = max((p for p in probs if p[5] == fs), key=lambda p: p[4])
         _, f, d_img, out, side, _ = big
         pr = ct.problem_for(d_img, f, in_w=side + fs - 1)
@@ -712,7 +720,7 @@ def run_batch(args):
         return [a.elapsed_time(b) for a, b in ev]
 
     k = max(5, min(args.steps, 200))
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(dev.index or 0)
     clocks.start()
     tb0 = time.time()
     ms_batch = timed(batch_step, k, max(3, args.warmup), "batch_timed")
@@ -733,10 +741,12 @@ def run_batch(args):
     batch_step()
     stream.synchronize()
     snap = [out.clone() for (_, _, _, out, _, _) in probs]
-    plain_step()
-    stream.synchronize()
-    identical = all(torch.equal(a.view(torch.int32), out.view(torch.int32))
-                    for a, (_, _, _, out, _, _) in zip(snap, probs)) if plain_args else None
+    identical = None
+    if plain_args:
+        plain_step()
+        stream.synchronize()
+        identical = all(torch.equal(a.view(torch.int32), out.view(torch.int32))
+                        for a, (_, _, _, out, _, _) in zip(snap, probs))
 
     # end to end: pinned host images in, outputs out, every step
     h_imgs = [torch.from_numpy(img).pin_memory() for (img, *_rest) in probs]
@@ -753,43 +763,204 @@ def run_batch(args):
             stream.synchronize()
         te = (time.perf_counter() - te0) / e_steps
     t_b = statistics.mean(ms_batch)
-    t_p = statistics.mean(ms_plain)
     q = sorted(ms_batch)
     p99 = q[min(len(q) - 1, int(math.ceil(0.99 * len(q))) - 1)]
+    res = {
+        "k": k, "flops": flops, "shapes": shapes, "ms_batch": ms_batch, "t_b": t_b,
+        "p50": statistics.median(ms_batch), "p99": p99, "t_p": statistics.mean(ms_plain),
+        "t_pg": statistics.mean(ms_plain_graph), "t_persist": statistics.mean(ms_persist),
+        "identical": identical, "peak_s": peak_s, "te": te,
+        "h2d": int(sum(h.numel() * 4 for h in h_imgs)), "d2h": int(sum(h.numel() * 4 for h in h_outs)),
+        "binfo": binfo, "buckets": batch.buckets(), "plan_s": batch_plan_s, "plain_tune_s": plain_tune_s,
+        "tuning": tuning, "clocks": clocks.summary(tb0, tb1),
+        # host copies of the batched outputs, for the CPU leg's check
+        "results": [(img, f, snap_k[:, :side].cpu().numpy(), side, fs)
+                    for (img, f, _, _, side, fs), snap_k in zip(probs, snap)],
+    }
+    del batch, persistent
+    return res
+
+
+def cpu_baseline_batch(results, seconds):
+    """The oracle over whole problems of the batched workload (all host
+    cores), largest first, until `seconds` of CPU work; each problem it
+    computes is compared pixel by pixel with the batched GPU output."""
+    import numpy as np
+    import oracle
+    order = sorted(range(len(results)), key=lambda i: -results[i][3])
+    t_total, flops, n, worst, ok, npx = 0.0, 0.0, 0, 0.0, True, 0
+    for i in order:
+        img, f, got, side, fs = results[i]
+        t = time.perf_counter()
+        ref, S = oracle.corr2d_f64(img, f, side, side)
+        t_total += time.perf_counter() - t
+        pr = parity_record(got, ref, S, "")
+        worst = max(worst, pr["max_err_over_S"])
+        ok = ok and pr["ok"]
+        npx += pr["n"]
+        flops += 2.0 * side * side * fs * fs
+        n += 1
+        if t_total >= seconds:
+            break
+    return {"value": flops / max(t_total, 1e-9) / 1e9, "unit": "GFLOP/s", "cores": oracle.max_threads(),
+            "kind": "oracle", "sample": f"{n} of {len(results)} problems of the batch, largest first, "
+                                        f"{t_total:.1f} s of FP64 CPU work",
+            "parity": {"n": npx, "problems": n, "max_err_over_S": worst, "bound": 1e-5, "ok": bool(ok),
+                       "over": f"every pixel of {n} of {len(results)} problems (largest first)"}}
+
+
+BF16_CASES = ((4096, 4096, 17, 4), (1024, 1024, 9, 4))   # (out_w, out_h, filter, seed)
+
+
+def measure_bf16(args, ct, dev, info, fp32_peak, case):
+    """BF16 storage, FP32 accumulation: a separate tuning run (annealing over
+    the full space) and the timed tuned and default configurations, L2
+    flushed between timed launches.  Returns the record and, for the CPU
+    leg, the inputs and both outputs."""
+    import numpy as np
+    import torch
+    import synthetic
+    ow, oh, fs, seed = case
+    img32, f32 = synthetic.make_problem(seed, ow, oh, fs, fs, pitch_align=8)
+    img_t = torch.from_numpy(img32).to(torch.bfloat16)
+    f_t = torch.from_numpy(np.ascontiguousarray(f32)).to(torch.bfloat16)
+    d_img = img_t.to(dev)
+    p = ct.problem_for(d_img, f_t, in_w=ow + fs - 1)
+    d_out = torch.empty((oh, p.out_pitch), dtype=torch.float32, device=dev)
+    t0 = time.time()
+    tab = ct.tune(p, "full", "anneal", image=d_img, filt=f_t, out=d_out, seed=args.seed,
+                  max_evals=args.bf16_evals, anneal_chains=args.anneal_chains)
+    tune_s = time.time() - t0
+    hf = ct._filter_bytes(f_t, p.dtype)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(int(2 * max(info.l2_bytes, 64 << 20)), dtype=torch.uint8, device=dev)
+    flops = 2.0 * ow * oh * fs * fs
+    res = {}
+    outs = {}
+    for name, cfg in (("tuned", tab.best), ("default", ct.default_config())):
+        k = max(10, min(args.steps, 100))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                ct.conv2d_raw(p, cfg, d_img.data_ptr(), hf, d_out.data_ptr(), stream.cuda_stream)
+            for i in range(k):
+                flush.fill_(i & 0xFF)
+                ev[i][0].record(stream)
+                ct.conv2d_raw(p, cfg, d_img.data_ptr(), hf, d_out.data_ptr(), stream.cuda_stream)
+                ev[i][1].record(stream)
+            stream.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        t = statistics.mean(ms)
+        res[name] = {"config": cfg.as_dict(), "ms": t, "ms_median": statistics.median(ms),
+                     "gflops": flops / (t * 1e-3) / 1e9, "frac_fp32_peak": flops / (t * 1e-3) / 1e12 / fp32_peak}
+        outs[name] = d_out[:, :ow].cpu().numpy()
+    ct.device_check()
+    rec = {"workload": f"corr2d out {ow}x{oh}, filter {fs}x{fs}, BF16 image and filter (round to nearest "
+                       f"even from uniform[-1,1) seed {seed}), FP32 accumulation and output",
+           "tuning": {"strategy": "anneal", "evals": tab.info["n_rows"], "wall_s": tune_s,
+                      "space_valid": tab.info["n_valid_space"]},
+           **res}
+    h_img_bits = img_t.view(torch.int16).numpy().view(np.uint16)
+    h_f_bits = f_t.view(torch.int16).numpy().view(np.uint16)
+    return rec, (img32, np.ascontiguousarray(f32), h_img_bits, np.ascontiguousarray(h_f_bits), ow, oh, outs)
+
+
+def cpu_baseline_bf16(data):
+    """The oracle on a BF16 case: FP64 on the BF16 values (parity of both
+    configurations, 1e-5 * S), and FP64 on the original FP32 values (the
+    error BF16 storage costs: max |gpu - exact| / S and the RMS error
+    relative to the RMS of the exact result), every pixel."""
+    import numpy as np
+    import oracle
+    img32, f32, img_bits, f_bits, ow, oh, outs = data
+    t = time.perf_counter()
+    ref32, S32 = oracle.corr2d_f64(img32, f32, ow, oh)
+    t32 = time.perf_counter() - t
+    refb, Sb = oracle.corr2d_bf16_f64(img_bits, f_bits, ow, oh)
+    fh, fw = f32.shape
+    rec = {"oracle_gflops": 2.0 * ow * oh * fw * fh / t32 / 1e9, "cores": oracle.max_threads()}
+    rms_exact = float(np.sqrt(np.mean(ref32 * ref32)))
+    for name, got in outs.items():
+        d = got.astype(np.float64) - ref32
+        with np.errstate(divide="ignore", invalid="ignore"):
+            rel = np.where(S32 > 0, np.abs(d) / S32, 0.0)
+        rec[name] = {"parity_vs_bf16_oracle": parity_record(got, refb, Sb, f"all {ow}x{oh} pixels"),
+                     "max_err_over_S_vs_fp32_inputs": float(rel.max()),
+                     "rms_err_rel_vs_fp32_inputs": float(np.sqrt(np.mean(d * d))) / rms_exact}
+    return rec
+
+
+def batch_workload_name():
+    return (f"{BATCH['count']} uneven FP32 correlations, square sides log-uniform in "
+            f"[{BATCH['side_lo']},{BATCH['side_hi']}], filters {list(BATCH['filters'])}, seed {BATCH['seed']}")
+
+
+def setup(args, need_dist=True):
+    """Process group (N > 1), device, the in-tree library, its cubin cache and
+    the FP32 peak; returns (ct, dev, info, peaks, fp32_peak, sm_max_mhz)."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1 and need_dist:
+        import datetime
+        import torch.distributed as dist
+        # the other ranks wait in a broadcast while rank 0 tunes (minutes)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
+                                timeout=datetime.timedelta(minutes=30))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2407_11488_gb300 import build as _build
+    if local == 0:
+        _build.build()
+    if world > 1 and need_dist:
+        torch.distributed.barrier()
+    import paper_2407_11488_gb300 as ct
+    ct.set_cache_dir(args.cache_dir or os.path.join(tempfile.gettempdir(), f"convtune-cache-{os.getuid()}"))
+    info = ct.device_query()
+    pk = peaks()
+    sm_max_mhz = float(pk.get("sm_max_mhz") or (info.clock_max_khz / 1e3) or 2070.0)
+    fp32_peak = info.sm_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12   # TFLOP/s
+    return ct, dev, info, pk, fp32_peak, sm_max_mhz
+
+
+def run_batch(args):
+    """The batched workload as the line's own metric (see measure_batch)."""
+    rank, world, local = dist_env()
+    ct, dev, info, pk, fp32_peak, sm_max_mhz = setup(args)
+    m = measure_batch(args, ct, dev, info, pk, fp32_peak, world)
+    flops, t_b, t_p = m["flops"], m["t_b"], m["t_p"]
     achieved = flops / (t_b * 1e-3) / 1e12
+    binfo = m["binfo"]
     line = {
         "metric": METRIC, "value": world * flops / (t_b * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": world,
-        "steps": k, "warmup": args.warmup, "ms_per_step": t_b, "higher_is_better": True, "scaling": "weak",
+        "steps": m["k"], "warmup": args.warmup, "ms_per_step": t_b, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{BATCH['count']} uneven FP32 correlations, square sides log-uniform in "
-                               f"[{BATCH['side_lo']},{BATCH['side_hi']}], filters {list(BATCH['filters'])}, "
-                               f"seed {BATCH['seed']}",
-                   "total_gflop": flops / 1e9, "l2": "flushed between timed iterations",
-                   "filter_subset": args.batch_filter or None,
+        "config": {"workload": batch_workload_name(), "total_gflop": flops / 1e9,
+                   "l2": "flushed between timed iterations", "filter_subset": args.batch_filter or None,
                    "parallelism": f"replicas x{world}"},
-        "batched_p50_ms": statistics.median(ms_batch), "batched_p99_ms": p99,
+        "batched_p50_ms": m["p50"], "batched_p99_ms": m["p99"],
         "plain_gflops": world * flops / (t_p * 1e-3) / 1e9, "plain_ms_per_step": t_p,
-        "batched_vs_plain": t_p / t_b, "bit_identical_to_plain": identical,
-        "plain_graph_ms_per_step": statistics.mean(ms_plain_graph),
-        "batched_vs_plain_graph": statistics.mean(ms_plain_graph) / t_b,
-        "persistent_only_ms_per_step": statistics.mean(ms_persist),
-        "persistent_only_vs_plain": t_p / statistics.mean(ms_persist),
-        "composite_bound_ms": peak_s * 1e3, "batched_frac_of_bound": peak_s * 1e3 / t_b,
-        "batch": {"buckets": batch.buckets(), **binfo, "plan_s": batch_plan_s},
-        "plain_tuning": {"wall_s": plain_tune_s, **tuning},
+        "batched_vs_plain": t_p / t_b, "bit_identical_to_plain": m["identical"],
+        "plain_graph_ms_per_step": m["t_pg"], "batched_vs_plain_graph": m["t_pg"] / t_b,
+        "persistent_only_ms_per_step": m["t_persist"], "persistent_only_vs_plain": t_p / m["t_persist"],
+        "composite_bound_ms": m["peak_s"] * 1e3, "batched_frac_of_bound": m["peak_s"] * 1e3 / t_b,
+        "batch": {"buckets": m["buckets"], **binfo, "plan_s": m["plan_s"]},
+        "plain_tuning": {"wall_s": m["plain_tune_s"], **m["tuning"]},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": None,
                      "peak_basis": f"{info.sm_count} SMs x {FP32_LANES_PER_SM} x 2 x {sm_max_mhz:.0f} MHz"},
-        "e2e": {"value": world * flops / te / 1e9, "unit": "GFLOP/s",
-                "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in h_imgs)),
-                "d2h_bytes_per_step": int(sum(h.numel() * 4 for h in h_outs)), "ms_per_step": te * 1e3},
-        "gpu_launches": k * (binfo["n_solo"] + (1 if binfo["n_work"] > 0 else 0)),
-        "clocks": clocks.summary(tb0, tb1),
+        "e2e": {"value": world * flops / m["te"] / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": m["h2d"],
+                "d2h_bytes_per_step": m["d2h"], "ms_per_step": m["te"] * 1e3},
+        "gpu_launches": m["k"] * (binfo["n_solo"] + (1 if binfo["n_work"] > 0 else 0)),
+        "clocks": m["clocks"],
         "device": info.name.decode(),
     }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_batch(m["results"], args.cpu_seconds)
+        line["parity"] = line["cpu_baseline"].pop("parity")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
+        import torch
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return 0
