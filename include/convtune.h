@@ -83,11 +83,27 @@ typedef struct {
  * tile_size_x, tile_size_y, use_shmem; unroll is Sec. 3's loop unrolling).
  * block_x * block_y <= 1024; 1 <= tile_x, tile_y <= 16; use_smem in {0, 1};
  * unroll in {0, 1}.  With use_smem = 1, block_x * tile_x must be a multiple
- * of 4 (the staged tile starts on a 16-byte boundary). */
+ * of 4 (the staged tile starts on a 16-byte boundary).
+ *
+ * persist and taps are not points of the search space but forms of a
+ * variant.  persist is chosen at launch (the same compiled variant serves both
+ * values): 0 launches one block per output tile; 1 launches as many blocks as
+ * the GPU holds at once, each computing every G-th tile in row-major tile
+ * order (G = that block count).  ct_tune times both when
+ * ct_tune_opts.grid_modes asks for it and reports the faster in each row.
+ * taps chooses where the filter lives: 0 in the launch's parameter block (one
+ * compiled variant serves every filter of the size); 1 compiled into the
+ * variant as immediate operands of the multiply-adds (one variant per filter:
+ * the first call with a new filter compiles it; the arithmetic and therefore
+ * the result bits are the same).  taps = 1 applies to unroll = 1 variants
+ * with finite taps; elsewhere it acts as 0.  ct_tune measures unrolled
+ * configurations with taps = 1 when ct_tune_opts.taps_imm is set. */
 typedef struct {
     int32_t block_x, block_y;
     int32_t tile_x, tile_y;
     int32_t use_smem, unroll;
+    int32_t persist;       /* 0: one block per tile; 1: persistent grid */
+    int32_t taps;          /* 0: taps in the parameter block; 1: compiled into the variant */
 } ct_config;
 
 /* Per-variant build facts (from the NVRTC/ptxas log and the launch shape). */
@@ -150,11 +166,19 @@ CT_API ct_status ct_default_config(const ct_problem* p, ct_config* out);
  * Table 1 values). */
 CT_API ct_status ct_check_config(const ct_problem* p, const ct_config* c, int32_t smem_limit_bytes);
 
-/* Compiles (or finds in a cache) the variant for (p, c) without loading it.
+/* Compiles (or finds in a cache) the variant for (p, c) without loading it,
+ * in the form that keeps the taps in the parameter block (c->taps is not
+ * looked at: there is no filter here).
  * Runs on a machine without a GPU: NVRTC targets sm_103a directly.  Paper:
  * Sec. 3 (the runner compiles the kernel source with the configuration's
  * parameter values, including unroll factors, as compile-time constants). */
 CT_API ct_status ct_compile(const ct_problem* p, const ct_config* c, ct_variant_info* info);
+/* Compiles (or finds in a cache) the variant that ct_conv2d runs for
+ * (p, c, h_filter) without loading it: with c->taps = 1 the one specific to
+ * this filter, so that a first ct_conv2d call with it does not wait for the
+ * compile.  Paper: Sec. 3 (compile per configuration). */
+CT_API ct_status ct_compile_filter(const ct_problem* p, const ct_config* c, const void* h_filter,
+                                   ct_variant_info* info);
 
 /* ---- the correlation ---------------------------------------------------- */
 
@@ -278,6 +302,21 @@ typedef struct {
                                  new rows are appended (NULL: none) */
     const char* trace_path;   /* ANNEAL: JSONL trace of every walker step, restart
                                  and start point, appended (NULL: none) */
+    int32_t grid_modes;       /* 0: time one block per tile only; 1: also time the
+                                 persistent grid (cfg.persist = 1) whenever the
+                                 problem has more tiles than the GPU holds at once,
+                                 and keep the faster (same compile, one more timing) */
+    int32_t remeasure_top;    /* > 0: after the strategy, measure the k fastest
+                                 configurations again, interleaved, with
+                                 remeasure_repeats launches each, and rank them by
+                                 those times (ct_table_info.remeasured) */
+    int32_t remeasure_repeats;/* launches per re-measured configuration (0: 31) */
+    int32_t taps_imm;         /* 1: measure every unroll = 1 configuration with the
+                                 problem's taps compiled in (cfg.taps = 1 in its row);
+                                 the compiles are then specific to this filter */
+    int32_t remeasure_taps;   /* 1: the re-measurement times each unrolled candidate in
+                                 both tap forms and keeps the faster (cfg.taps) */
+    int32_t reserved3;
 } ct_tune_opts;
 
 /* One row of a timing table. */
@@ -291,6 +330,12 @@ typedef struct {
     int32_t regs, spill_bytes, smem_bytes;
     int32_t eval_order;       /* 0-based order in which the strategy measured it */
     double compile_ms;
+    double t_tiles_ms;        /* median with one block per tile (cfg.persist = 0) */
+    double t_persist_ms;      /* median with the persistent grid (NaN: not timed);
+                                 t_med_ms is the smaller, cfg.persist says which */
+    double t_remeasured_ms;   /* median of the re-measurement (NaN: not re-measured) */
+    int32_t sm_mhz;           /* SM clock sampled right after the timing (0: unknown) */
+    int32_t reserved;
 } ct_row;
 
 typedef struct {
@@ -302,6 +347,10 @@ typedef struct {
     double compile_wall_ms;   /* wall time the benchmark loop waited on compiles */
     double compile_cpu_ms;    /* sum of NVRTC compile times */
     double bench_ms;          /* wall time spent launching and timing */
+    double remeasure_ms;      /* wall time of the re-measurement (0: none) */
+    int32_t remeasured;       /* configurations re-measured; when > 0, best_row is
+                                 the fastest of them by t_remeasured_ms */
+    int32_t sm_mhz_median;    /* median of the rows' sm_mhz samples (0: unknown) */
 } ct_table_info;
 
 typedef struct ct_table ct_table;
@@ -526,6 +575,9 @@ typedef struct {
     double wall_s;         /* first submit to last completion since the last reset */
     double req_per_s, gflops;
     int64_t peak_mem_bytes;
+    double kernel_busy_s;      /* time some launch's kernel was running (union of the intervals
+                                  between events recorded around each kernel) */
+    double kernel_busy_frac;   /* kernel_busy_s / wall_s */
 } ct_server_stats;
 
 typedef struct ct_server ct_server;
@@ -554,6 +606,29 @@ CT_API ct_status ct_server_wait(ct_server* s, uint64_t request_id, int64_t timeo
 CT_API ct_status ct_server_drain(ct_server* s, int64_t timeout_us);
 CT_API ct_status ct_server_stats_get(ct_server* s, ct_server_stats* out);
 CT_API ct_status ct_server_stats_reset(ct_server* s);
+/* A request stream driven from native threads, so that the caller's
+ * language does not set the rate: requests[k] is submitted at arrival_s[k]
+ * seconds after the start (open loop; NULL: as soon as allowed, closed loop),
+ * never with more than max_in_flight requests submitted and not yet
+ * collected; a second thread collects them in submission order (each wait
+ * bounded by timeout_us; < 0: none).  Requests that share an output buffer
+ * must be at least max_in_flight apart.  latency_ms (n values, may be NULL)
+ * receives each request's submit-to-done time (NaN when it failed). */
+typedef struct {
+    int64_t n;
+    const ct_request* requests;
+    const double* arrival_s;
+    int32_t max_in_flight;
+    int32_t reserved;
+    int64_t timeout_us;
+    double* latency_ms;
+} ct_server_run_opts;
+
+/* Waits until the server is idle, resets its statistics, runs the stream and
+ * returns the statistics of this run in *out (may be NULL).  Synchronous.
+ * Errors: the first failing submission's status, or CT_ERR_TIMEOUT when a
+ * wait ran out (the run stops submitting; submitted requests are collected). */
+CT_API ct_status ct_server_run(ct_server* s, const ct_server_run_opts* opts, ct_server_stats* out);
 /* Stops the dispatcher after the queued work finishes and frees everything. */
 CT_API void ct_server_destroy(ct_server* s);
 

@@ -41,14 +41,22 @@ class Problem(ctypes.Structure):
 
 
 class Config(ctypes.Structure):
+    """A point of the search space (the first six fields) plus two forms of
+    the variant: ``persist`` (0: one block per tile, 1: persistent grid) and
+    ``taps`` (0: taps in the parameter block, 1: compiled into the variant)."""
     _fields_ = [("block_x", i32), ("block_y", i32), ("tile_x", i32), ("tile_y", i32),
-                ("use_smem", i32), ("unroll", i32)]
+                ("use_smem", i32), ("unroll", i32), ("persist", i32), ("taps", i32)]
+    PARAMS = ("block_x", "block_y", "tile_x", "tile_y", "use_smem", "unroll", "persist", "taps")
 
     def as_dict(self):
-        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+        return {k: int(getattr(self, k)) for k in self.PARAMS}
 
     def as_tuple(self):
-        return tuple(int(getattr(self, k)) for k, _ in self._fields_)
+        return tuple(int(getattr(self, k)) for k in self.PARAMS)
+
+    def space_tuple(self):
+        """The six search-space parameters (without the grid choice)."""
+        return self.as_tuple()[:6]
 
     def __repr__(self):
         return "Config(%s)" % ", ".join(f"{k}={v}" for k, v in self.as_dict().items())
@@ -74,18 +82,21 @@ class TuneOpts(ctypes.Structure):
     _fields_ = [("seed", u64), ("sample_fraction", dbl), ("max_evals", i32), ("repeats", i32),
                 ("warmup", i32), ("flush_l2", i32), ("compile_threads", i32), ("graph_below_us", i32),
                 ("anneal_chains", i32), ("reserved", i32), ("cache_dir", cp), ("resume_path", cp),
-                ("trace_path", cp)]
+                ("trace_path", cp), ("grid_modes", i32), ("remeasure_top", i32), ("remeasure_repeats", i32),
+                ("taps_imm", i32), ("remeasure_taps", i32), ("reserved3", i32)]
 
 
 class Row(ctypes.Structure):
     _fields_ = [("cfg", Config), ("index", i64), ("status", i32), ("n", i32), ("t_med_ms", dbl),
                 ("t_min_ms", dbl), ("t_std_ms", dbl), ("gflops", dbl), ("regs", i32), ("spill_bytes", i32),
-                ("smem_bytes", i32), ("eval_order", i32), ("compile_ms", dbl)]
+                ("smem_bytes", i32), ("eval_order", i32), ("compile_ms", dbl), ("t_tiles_ms", dbl),
+                ("t_persist_ms", dbl), ("t_remeasured_ms", dbl), ("sm_mhz", i32), ("reserved", i32)]
 
 
 class TableInfo(ctypes.Structure):
     _fields_ = [("strategy", i32), ("n_rows", i32), ("n_valid_space", i64), ("best_row", i64),
-                ("wall_ms", dbl), ("compile_wall_ms", dbl), ("compile_cpu_ms", dbl), ("bench_ms", dbl)]
+                ("wall_ms", dbl), ("compile_wall_ms", dbl), ("compile_cpu_ms", dbl), ("bench_ms", dbl),
+                ("remeasure_ms", dbl), ("remeasured", i32), ("sm_mhz_median", i32)]
 
 
 class BatchItem(ctypes.Structure):
@@ -124,7 +135,13 @@ class Request(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", i64), ("completed", i64), ("failed", i64), ("launches", i64), ("mean_batch", dbl),
                 ("p50_ms", dbl), ("p99_ms", dbl), ("mean_ms", dbl), ("max_ms", dbl), ("wall_s", dbl),
-                ("req_per_s", dbl), ("gflops", dbl), ("peak_mem_bytes", i64)]
+                ("req_per_s", dbl), ("gflops", dbl), ("peak_mem_bytes", i64), ("kernel_busy_s", dbl),
+                ("kernel_busy_frac", dbl)]
+
+
+class ServerRunOpts(ctypes.Structure):
+    _fields_ = [("n", i64), ("requests", ctypes.c_void_p), ("arrival_s", ctypes.c_void_p), ("max_in_flight", i32),
+                ("reserved", i32), ("timeout_us", i64), ("latency_ms", ctypes.c_void_p)]
 
 
 class Analysis(ctypes.Structure):
@@ -143,6 +160,7 @@ _SIGS = {
     "ct_default_config": (i32, [P(Problem), P(Config)]),
     "ct_check_config": (i32, [P(Problem), P(Config), i32]),
     "ct_compile": (i32, [P(Problem), P(Config), P(VariantInfo)]),
+    "ct_compile_filter": (i32, [P(Problem), P(Config), vp, P(VariantInfo)]),
     "ct_device_check": (i32, [i32]),
     "ct_conv2d": (i32, [P(Problem), P(Config), vp, vp, vp, vp]),
     "ct_conv2d_host": (i32, [P(Problem), P(Config), vp, vp, vp, vp, vp, vp]),
@@ -177,6 +195,7 @@ _SIGS = {
     "ct_server_drain": (i32, [vp, i64]),
     "ct_server_stats_get": (i32, [vp, P(ServerStats)]),
     "ct_server_stats_reset": (i32, [vp]),
+    "ct_server_run": (i32, [vp, P(ServerRunOpts), P(ServerStats)]),
     "ct_server_destroy": (None, [vp]),
 }
 EXPORTED = tuple(_SIGS)
@@ -242,8 +261,8 @@ def clear_cache():
     _check(_load().ct_clear_cache())
 
 
-def config(block_x=32, block_y=8, tile_x=1, tile_y=1, use_smem=0, unroll=0) -> Config:
-    return Config(block_x, block_y, tile_x, tile_y, use_smem, unroll)
+def config(block_x=32, block_y=8, tile_x=1, tile_y=1, use_smem=0, unroll=0, persist=0, taps=0) -> Config:
+    return Config(block_x, block_y, tile_x, tile_y, use_smem, unroll, persist, taps)
 
 
 def default_config() -> Config:
@@ -268,11 +287,17 @@ def check_config(problem: Problem, cfg: Config, smem_limit: int = 0):
     _check(_load().ct_check_config(ctypes.byref(problem), ctypes.byref(cfg), smem_limit))
 
 
-def compile_variant(problem: Problem, cfg: Config) -> dict:
+def compile_variant(problem: Problem, cfg: Config, filt=None) -> dict:
     """Compiles the variant (NVRTC → sm_103a cubin) without loading it; works
-    without a GPU.  Returns the ptxas facts."""
+    without a GPU.  With ``filt`` (host filter) the variant ct_conv2d runs for
+    that filter (filter-specific when cfg.taps = 1).  Returns the ptxas facts."""
     info = VariantInfo()
-    _check(_load().ct_compile(ctypes.byref(problem), ctypes.byref(cfg), ctypes.byref(info)))
+    if filt is None:
+        _check(_load().ct_compile(ctypes.byref(problem), ctypes.byref(cfg), ctypes.byref(info)))
+    else:
+        fb = _filter_bytes(filt, problem.dtype)
+        _check(_load().ct_compile_filter(ctypes.byref(problem), ctypes.byref(cfg), fb.ctypes.data_as(vp),
+                                         ctypes.byref(info)))
     return {k: getattr(info, k) for k, _ in VariantInfo._fields_ if k != "reserved"}
 
 
@@ -444,7 +469,7 @@ class Table:
 
 
 def _row_dict(r: Row) -> dict:
-    d = {k: getattr(r, k) for k, _ in Row._fields_ if k != "cfg"}
+    d = {k: getattr(r, k) for k, _ in Row._fields_ if k not in ("cfg", "reserved")}
     d["cfg"] = Config(*r.cfg.as_tuple())
     d.update(r.cfg.as_dict())
     return d
@@ -484,10 +509,12 @@ def _collect(t, best, write_path=None, space=None, flops=0.0) -> Table:
 
 
 def _opts(seed=0, sample_fraction=0.0, max_evals=0, repeats=0, warmup=0, flush_l2=False, compile_threads=0,
-          graph_below_us=0, anneal_chains=0, cache_dir=None, resume_path=None, trace_path=None):
+          graph_below_us=0, anneal_chains=0, cache_dir=None, resume_path=None, trace_path=None, grid_modes=0,
+          remeasure_top=0, remeasure_repeats=0, taps_imm=0, remeasure_taps=0):
     return TuneOpts(seed, sample_fraction, max_evals, repeats, warmup, int(flush_l2), compile_threads,
                     graph_below_us, anneal_chains, 0, cache_dir.encode() if cache_dir else None,
-                    resume_path.encode() if resume_path else None, trace_path.encode() if trace_path else None)
+                    resume_path.encode() if resume_path else None, trace_path.encode() if trace_path else None,
+                    int(grid_modes), remeasure_top, remeasure_repeats, int(taps_imm), int(remeasure_taps), 0)
 
 
 def tune(problem: Problem, space="small", strategy="brute", *, image=None, filt=None, out=None,
@@ -616,6 +643,7 @@ class Server:
         self.handle = h
         self.dtype = dtype
         self._refs = {}
+        self._fcache = {}   # filter object id -> (filter, its bytes), for run() requests
 
     def register_image(self, h_image, in_w=None) -> int:
         """Uploads a host image tensor (in_h, in_pitch) that stays resident."""
@@ -659,6 +687,35 @@ class Server:
 
     def reset_stats(self):
         _check(_load().ct_server_stats_reset(self.handle))
+
+    def request(self, h_out, filt, out_w, out_h, *, h_image=None, image_id=0, in_pitch=None) -> Request:
+        """A request record for run(); the filter bytes are kept alive by the server object."""
+        key = id(filt)
+        hit = self._fcache.get(key)
+        if hit is None or hit[0] is not filt:
+            hit = (filt, _filter_bytes(filt, self.dtype))
+            self._fcache[key] = hit
+        fb = hit[1]
+        fh, fw = fb.shape
+        if in_pitch is None:
+            in_pitch = int(h_image.stride(0)) if h_image is not None else 0
+        return Request(ctypes.c_void_p(h_image.data_ptr()) if h_image is not None else None, image_id,
+                       ctypes.c_void_p(h_out.data_ptr()), fb.ctypes.data_as(vp), out_w, out_h, fw, fh, in_pitch,
+                       int(h_out.stride(0)))
+
+    def run(self, requests, *, arrival_s=None, max_in_flight=64, timeout_us=120_000_000):
+        """ct_server_run: submit `requests` (a list of Request, or a ctypes array)
+        from native threads, paced by arrival_s (seconds from the start) or
+        closed loop; returns (stats dict, latencies in ms as a numpy array)."""
+        n = len(requests)
+        arr = requests if isinstance(requests, ctypes.Array) else (Request * n)(*requests)
+        lat = np.full(n, np.nan)
+        arrivals = None if arrival_s is None else np.ascontiguousarray(arrival_s, dtype=np.float64)
+        o = ServerRunOpts(n, ctypes.cast(arr, vp), arrivals.ctypes.data if arrivals is not None else None,
+                          max_in_flight, 0, timeout_us, lat.ctypes.data)
+        st = ServerStats()
+        _check(_load().ct_server_run(self.handle, ctypes.byref(o), ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}, lat
 
     def close(self):
         if getattr(self, "handle", None) and _lib is not None:

@@ -20,7 +20,8 @@ BUILD = os.path.join(PKG, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libconvtune.so")
 
-CPP = ["common.cpp", "variant.cpp", "tune.cpp", "capi.cpp", "batch.cpp", "serve.cpp", "analyze.cpp"]
+CPP = ["common.cpp", "variant.cpp", "tune.cpp", "capi.cpp", "batch.cpp", "serve.cpp", "analyze.cpp",
+       "clocks.cpp"]
 CU = ["aux_kernels.cu", "noalloc.cu"]
 HEADERS = ["ct_internal.hpp", "batch_internal.hpp", "corr2d.cuh", "batch.cuh"]
 GENCODE = "-gencode=arch=compute_103a,code=sm_103a"

@@ -411,7 +411,9 @@ ct_status plan_solo(ct_batch& B, const ct_batch_opts& o, std::vector<char>& solo
             return fail(st, "tuning the single-problem configuration for filter %dx%d: %s", big.filter_w,
                         big.filter_h, last_error());
         if (st != CT_OK) continue;   // no configuration ran: this size stays in the persistent launch
-        VariantPtr v = compile_variant(VariantKey{best, big.filter_w, big.filter_h, B.dtype}, cache_dir_setting());
+        // one variant per filter size, shared by problems with different filters: taps in the parameter block
+        best.taps = 0;
+        VariantPtr v = compile_variant(variant_key(p, best, nullptr), cache_dir_setting());
         if (!v || v->status != CT_OK)
             return fail(CT_ERR_COMPILE, "single-problem variant: %s", v ? v->error.c_str() : "no variant");
         if ((st = load_variant(*v)) != CT_OK) return st;
@@ -661,7 +663,9 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
         for (size_t k = 0; k < B->solo_items.size() && st == CT_OK; ++k) {
             const ct_batch_item& it = items[B->solo_items[k]];
             const ct_problem p{it.out_w, it.out_h, it.filter_w, it.filter_h, it.in_pitch, it.out_pitch, o.dtype, 0};
-            st = launch_variant(*B->solo_vars[k], p, it.d_image, it.h_filter, it.d_out, forks.streams[k % nfs]);
+            // one block per tile: the solo launches run beside each other, and
+            // small blocks let the hardware interleave them
+            st = launch_variant(*B->solo_vars[k], p, it.d_image, it.h_filter, it.d_out, forks.streams[k % nfs], 0);
         }
         for (size_t k = 0; k < nfs; ++k) {
             cudaEventRecord(forks.events[k + 1], forks.streams[k]);

@@ -71,11 +71,17 @@ CT_API ct_status ct_check_config(const ct_problem* p, const ct_config* c, int32_
 
 CT_API ct_status ct_compile(const ct_problem* p, const ct_config* c, ct_variant_info* info)
 {
+    return ct_compile_filter(p, c, nullptr, info);
+}
+
+CT_API ct_status ct_compile_filter(const ct_problem* p, const ct_config* c, const void* h_filter,
+                                   ct_variant_info* info)
+{
     ct_status s = check_problem(p);
     if (s != CT_OK) return s;
     if (!c) return fail(CT_ERR_INVALID_ARG, "config is NULL");
     if ((s = check_config(*p, *c, kDefaultSmemLimit)) != CT_OK) return s;
-    VariantPtr v = get_variant(VariantKey{*c, p->filter_w, p->filter_h, p->dtype});
+    VariantPtr v = get_variant(variant_key(*p, *c, h_filter));
     if (info) {
         memset(info, 0, sizeof *info);
         info->regs = v->regs;
@@ -113,9 +119,9 @@ CT_API ct_status ct_conv2d(const ct_problem* p, const ct_config* c, const void* 
     if ((s = require_device()) != CT_OK) return s;
     if ((s = check_config(*p, *c, 0)) != CT_OK) return s;
     if (p->out_w == 0 || p->out_h == 0) return CT_OK;
-    VariantPtr v = get_variant(VariantKey{*c, p->filter_w, p->filter_h, p->dtype});
+    VariantPtr v = get_variant(variant_key(*p, *c, h_filter));
     if (v->status != CT_OK) return fail((ct_status)v->status, "%s", v->error.c_str());
-    return launch_variant(*v, *p, d_image, h_filter, d_out, (cudaStream_t)stream);
+    return launch_variant(*v, *p, d_image, h_filter, d_out, (cudaStream_t)stream, c->persist);
 }
 
 // Streams and events of the host-buffer pipeline, one set per device.
@@ -151,7 +157,7 @@ static ct_status host_pipeline(const ct_problem* p, const ct_config* c, const vo
     if ((s = check_buffers(*p, d_image_ws, h_filter, d_out_ws)) != CT_OK) return s;
     if ((s = require_device()) != CT_OK) return s;
     if ((s = check_config(*p, *c, 0)) != CT_OK) return s;
-    VariantPtr v = get_variant(VariantKey{*c, p->filter_w, p->filter_h, p->dtype});
+    VariantPtr v = get_variant(variant_key(*p, *c, h_filter));
     if (v->status != CT_OK) return fail((ct_status)v->status, "%s", v->error.c_str());
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -203,7 +209,7 @@ static ct_status host_pipeline(const ct_problem* p, const ct_config* c, const vo
         ct_problem pb = *p;
         pb.out_h = (int32_t)(y1 - y0);
         if ((s = launch_variant(*v, pb, (const char*)d_image_ws + y0 * p->in_pitch * es, h_filter,
-                                d_out_ws + y0 * p->out_pitch, cs)) != CT_OK)
+                                d_out_ws + y0 * p->out_pitch, cs, c->persist)) != CT_OK)
             return s;
         cudaEventRecord(e_comp, cs);
         cudaStreamWaitEvent(hp.copy_out, e_comp, 0);

@@ -31,6 +31,10 @@
 //                  0: the loop over filter rows stays rolled
 //   CT_FW, CT_FH   filter width and height
 //   CT_DTYPE       0: FP32 image; 1: BF16 image (widened to FP32 on load)
+//   CT_TAPS_IMM    1 (with CT_UNROLL = 1): the taps are compiled in, from
+//                  CT_TAP_VALUES (FH*FW float literals, row-major), so every
+//                  multiply-add takes its tap as an immediate operand; 0: the
+//                  taps come from the parameter block
 //
 // Layout contract (checked by the host before launch): row pitches are in
 // elements and make every row start on a 16-byte boundary; the image buffer
@@ -38,7 +42,13 @@
 // in the kernel's parameter block (constant bank), so FFMAs take them as
 // uniform operands with no load instruction.  A wait for the tensor copy
 // gives up after about two seconds: the block then sets bit 0 of the error
-// word, waits (again bounded) for the copy, and stores nothing.
+// word, waits (again bounded) for the copy, and stores nothing more.
+//
+// Grid (a launch-time choice, the same cubin): either one block per output
+// tile (a 2-D grid of tiles_x x tiles_y blocks), or persistent (p.persist = 1:
+// a 1-D grid of as many blocks as the GPU holds at once; block b computes
+// tiles b, b + G, b + 2G, ... in row-major tile order, G = gridDim.x), which
+// spreads the last partial wave of tiles evenly over the SMs.
 
 #ifndef CT_DTYPE
 #define CT_DTYPE 0
@@ -53,6 +63,13 @@
 // nonzero value makes the wait run out.  0 in every normal build.
 #ifndef CT_TEST_EXTRA_TX
 #define CT_TEST_EXTRA_TX 0
+#endif
+
+#ifndef CT_TAPS_IMM
+#define CT_TAPS_IMM 0
+#endif
+#if CT_TAPS_IMM && !CT_UNROLL
+#error "compiled-in taps need the unrolled body"
 #endif
 
 #ifdef CT_INJECT_COMPILE_ERROR
@@ -81,6 +98,11 @@ struct CtParams {
     int out_w, out_h;
     int in_w, in_h;
     unsigned* err;      // error word
+    int tiles_x;        // tile columns
+    int n_tiles;        // tiles in all
+    int persist;        // 1: persistent 1-D grid (see above)
+    int step_x, step_y; // persistent: gridDim.x as (tile columns, tile rows) of the row-major order
+    int pad_;
     float f[CT_FH * CT_FW];
 };
 
@@ -159,13 +181,16 @@ __device__ __forceinline__ void ct_row_global(float (&w)[CT_WWV], const CtParams
 
 #if CT_TMA
 __device__ __forceinline__ unsigned ct_sa(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+// One test of the barrier phase; a thread whose phase has not completed is
+// suspended until it does or up to about 0.1 ms (the suspend-time hint), so
+// a waiting warp issues few instructions.
 __device__ __forceinline__ bool ct_bar_try_wait(unsigned long long* bar, unsigned parity)
 {
     unsigned done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(ct_sa(bar)), "r"(parity)
+        : "r"(ct_sa(bar)), "r"(parity), "r"(100000u)
         : "memory");
     return done != 0;
 }
@@ -205,10 +230,19 @@ ct_corr2d(const __grid_constant__ CtParams p)
 {
     const int lx = threadIdx.x * CT_TX;
     const int ly = threadIdx.y * CT_TY;
-    const int gx0 = blockIdx.x * CT_TILE_W;
-    const int gy0 = blockIdx.y * CT_TILE_H;
-    const int gx = gx0 + lx;
-    const int gy = gy0 + ly;
+    // this block's first tile
+    int txi = blockIdx.x, tyi = blockIdx.y;
+    if (p.persist) {
+        tyi = blockIdx.x / p.tiles_x;
+        txi = blockIdx.x - tyi * p.tiles_x;
+    }
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+#if CT_TAPS_IMM
+    constexpr float ct_taps[CT_FH * CT_FW] = {CT_TAP_VALUES};
+#define CT_TAP(k) ct_taps[k]
+#else
+#define CT_TAP(k) p.f[k]
+#endif
 
 #if CT_SMEM && CT_TMA
     extern __shared__ float4 ct_smem4[];
@@ -216,128 +250,162 @@ ct_corr2d(const __grid_constant__ CtParams p)
     unsigned char* const raw = reinterpret_cast<unsigned char*>(ct_smem4);
     const unsigned mis = ct_sa(raw) & 127u;   // the tensor copy lands on a 128-byte boundary
     float* const sm = reinterpret_cast<float*>(raw + (mis ? 128u - mis : 0u));
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
+    if (lead) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(ct_sa(&ct_bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(ct_sa(&ct_bar)),
-                     "r"((unsigned)(CT_HALO_H * CT_SW * 4 + CT_TEST_EXTRA_TX))
-                     : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-            "[%4];\n" ::"r"(ct_sa(sm)),
-            "l"(&p.tmap), "r"(gx0), "r"(gy0), "r"(ct_sa(&ct_bar))
-            : "memory");
     }
     __syncthreads();   // the barrier is initialised before anyone waits on it
-    if (!ct_bar_wait(&ct_bar, 0u)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            atomicOr(p.err, 1u);
-            (void)ct_bar_wait(&ct_bar, 0u);
-        }
-        return;
-    }
+    unsigned phase = 0u;
 #define CT_LOAD_ROW(w, r) ct_row_shared(w, sm + (ly + (r)) * CT_SW + lx)
 #elif CT_SMEM
     extern __shared__ float4 ct_smem4[];
     float* sm = reinterpret_cast<float*>(ct_smem4);
-    {
-        // Stage rows gy0 .. gy0+HALO_H-1, columns gx0 .. gx0+SW-1 in 4-element
-        // chunks (16 bytes for FP32, 8 for BF16).  gx0 is a multiple of 16.
-        constexpr int CH = CT_SW / 4;
-        constexpr int NCH = CT_HALO_H * CH;
-        const int tid = threadIdx.y * CT_BX + threadIdx.x;
-#pragma unroll 4
-        for (int idx = tid; idx < NCH; idx += CT_NT) {
-            const int r = idx / CH;
-            const int c = (idx - r * CH) * 4;
-            const int yy = gy0 + r, xx = gx0 + c;
-            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (yy < p.in_h && xx < p.in_w) {
-                const ct_in_t* src = p.in + (ct_i64)yy * p.in_pitch + xx;
-#if CT_DTYPE == 0
-                v = __ldg(reinterpret_cast<const float4*>(src));
-#else
-                const uint2 u = __ldg(reinterpret_cast<const uint2*>(src));
-                v = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
-                                __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
-#endif
-            }
-            *reinterpret_cast<float4*>(sm + r * CT_SW + c) = v;
-        }
-    }
-    __syncthreads();
 #define CT_LOAD_ROW(w, r) ct_row_shared(w, sm + (ly + (r)) * CT_SW + lx)
 #else
 #define CT_LOAD_ROW(w, r) ct_row_global(w, p, gy + (r), gx)
 #endif
 
-    float acc[CT_TY][CT_TX];
+    for (int t = p.persist ? (int)blockIdx.x : 0;;) {
+        const int gx0 = txi * CT_TILE_W;
+        const int gy0 = tyi * CT_TILE_H;
+        const int gx = gx0 + lx;
+        const int gy = gy0 + ly;
+        bool ok = true;
+
+#if CT_SMEM && CT_TMA
+        if (lead) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(ct_sa(&ct_bar)),
+                         "r"((unsigned)(CT_HALO_H * CT_SW * 4 + CT_TEST_EXTRA_TX))
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                "%3}], [%4];\n" ::"r"(ct_sa(sm)),
+                "l"(&p.tmap), "r"(gx0), "r"(gy0), "r"(ct_sa(&ct_bar))
+                : "memory");
+        }
+        ok = ct_bar_wait(&ct_bar, phase);
+        if (!ok) {
+            atomicOr(p.err, 1u);
+            if (lead) (void)ct_bar_wait(&ct_bar, phase);   // the copy may still land: wait (bounded) before leaving
+        }
+        phase ^= 1u;
+#elif CT_SMEM
+        {
+            // Stage rows gy0 .. gy0+HALO_H-1, columns gx0 .. gx0+SW-1 in 4-element
+            // chunks (16 bytes for FP32, 8 for BF16).  gx0 is a multiple of 16.
+            constexpr int CH = CT_SW / 4;
+            constexpr int NCH = CT_HALO_H * CH;
+            const int tid = threadIdx.y * CT_BX + threadIdx.x;
+#pragma unroll 4
+            for (int idx = tid; idx < NCH; idx += CT_NT) {
+                const int r = idx / CH;
+                const int c = (idx - r * CH) * 4;
+                const int yy = gy0 + r, xx = gx0 + c;
+                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (yy < p.in_h && xx < p.in_w) {
+                    const ct_in_t* src = p.in + (ct_i64)yy * p.in_pitch + xx;
+#if CT_DTYPE == 0
+                    v = __ldg(reinterpret_cast<const float4*>(src));
+#else
+                    const uint2 u = __ldg(reinterpret_cast<const uint2*>(src));
+                    v = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                                    __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+#endif
+                }
+                *reinterpret_cast<float4*>(sm + r * CT_SW + c) = v;
+            }
+        }
+        __syncthreads();
+#endif
+
+        if (ok) {
+            float acc[CT_TY][CT_TX];
 #pragma unroll
-    for (int ty = 0; ty < CT_TY; ++ty)
+            for (int ty = 0; ty < CT_TY; ++ty)
 #pragma unroll
-        for (int tx = 0; tx < CT_TX; ++tx) acc[ty][tx] = 0.0f;
+                for (int tx = 0; tx < CT_TX; ++tx) acc[ty][tx] = 0.0f;
 
 #if CT_UNROLL
-    // Input row r feeds output rows ty with filter row i = r - ty.
+            // Input row r feeds output rows ty with filter row i = r - ty.
 #pragma unroll
-    for (int r = 0; r < CT_TY + CT_FH - 1; ++r) {
-        float w[CT_WWV];
-        CT_LOAD_ROW(w, r);
+            for (int r = 0; r < CT_TY + CT_FH - 1; ++r) {
+                float w[CT_WWV];
+                CT_LOAD_ROW(w, r);
 #pragma unroll
-        for (int ty = 0; ty < CT_TY; ++ty) {
-            const int i = r - ty;
-            if (i >= 0 && i < CT_FH) {
+                for (int ty = 0; ty < CT_TY; ++ty) {
+                    const int i = r - ty;
+                    if (i >= 0 && i < CT_FH) {
 #pragma unroll
-                for (int j = 0; j < CT_FW; ++j) {
-                    const float fv = p.f[i * CT_FW + j];
+                        for (int j = 0; j < CT_FW; ++j) {
+                            const float fv = CT_TAP(i * CT_FW + j);
 #pragma unroll
-                    for (int tx = 0; tx < CT_TX; ++tx)
-                        acc[ty][tx] = fmaf(w[tx + j], fv, acc[ty][tx]);
+                            for (int tx = 0; tx < CT_TX; ++tx)
+                                acc[ty][tx] = fmaf(w[tx + j], fv, acc[ty][tx]);
+                        }
+                    }
                 }
             }
-        }
-    }
 #else
 #pragma unroll 1
-    for (int i = 0; i < CT_FH; ++i) {
+            for (int i = 0; i < CT_FH; ++i) {
 #pragma unroll
-        for (int ty = 0; ty < CT_TY; ++ty) {
-            float w[CT_WWV];
-            CT_LOAD_ROW(w, ty + i);
+                for (int ty = 0; ty < CT_TY; ++ty) {
+                    float w[CT_WWV];
+                    CT_LOAD_ROW(w, ty + i);
 #pragma unroll
-            for (int j = 0; j < CT_FW; ++j) {
-                const float fv = p.f[i * CT_FW + j];
+                    for (int j = 0; j < CT_FW; ++j) {
+                        const float fv = CT_TAP(i * CT_FW + j);
 #pragma unroll
-                for (int tx = 0; tx < CT_TX; ++tx)
-                    acc[ty][tx] = fmaf(w[tx + j], fv, acc[ty][tx]);
-            }
-        }
-    }
-#endif
-#undef CT_LOAD_ROW
-
-#pragma unroll
-    for (int ty = 0; ty < CT_TY; ++ty) {
-        const int y = gy + ty;
-        if (y < p.out_h) {
-            float* __restrict__ orow = p.out + (ct_i64)y * p.out_pitch + gx;
-#if CT_TX % 4 == 0
-#pragma unroll
-            for (int k = 0; k < CT_TX; k += 4) {
-                if (gx + k + 3 < p.out_w) {
-                    *reinterpret_cast<float4*>(orow + k) =
-                        make_float4(acc[ty][k], acc[ty][k + 1], acc[ty][k + 2], acc[ty][k + 3]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (gx + k + e < p.out_w) orow[k + e] = acc[ty][k + e];
+                        for (int tx = 0; tx < CT_TX; ++tx)
+                            acc[ty][tx] = fmaf(w[tx + j], fv, acc[ty][tx]);
+                    }
                 }
             }
+#endif
+
+#pragma unroll
+            for (int ty = 0; ty < CT_TY; ++ty) {
+                const int y = gy + ty;
+                if (y < p.out_h) {
+                    float* __restrict__ orow = p.out + (ct_i64)y * p.out_pitch + gx;
+#if CT_TX % 4 == 0
+#pragma unroll
+                    for (int k = 0; k < CT_TX; k += 4) {
+                        if (gx + k + 3 < p.out_w) {
+                            *reinterpret_cast<float4*>(orow + k) =
+                                make_float4(acc[ty][k], acc[ty][k + 1], acc[ty][k + 2], acc[ty][k + 3]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (gx + k + e < p.out_w) orow[k + e] = acc[ty][k + e];
+                        }
+                    }
 #else
 #pragma unroll
-            for (int tx = 0; tx < CT_TX; ++tx)
-                if (gx + tx < p.out_w) orow[tx] = acc[ty][tx];
+                    for (int tx = 0; tx < CT_TX; ++tx)
+                        if (gx + tx < p.out_w) orow[tx] = acc[ty][tx];
 #endif
+                }
+            }
         }
+
+        // next tile (persistent grid only)
+        if (!p.persist) break;
+        t += gridDim.x;
+        if (t >= p.n_tiles) break;
+        txi += p.step_x;
+        tyi += p.step_y;
+        if (txi >= p.tiles_x) {
+            txi -= p.tiles_x;
+            ++tyi;
+        }
+#if CT_SMEM
+        // every thread is done with the staged tile (and agrees whether to go on)
+        if (__syncthreads_or(!ok)) break;
+#else
+        if (!ok) break;
+#endif
     }
+#undef CT_LOAD_ROW
+#undef CT_TAP
 }

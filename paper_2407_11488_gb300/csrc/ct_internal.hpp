@@ -88,9 +88,14 @@ std::vector<Entry> enumerate_valid(const Space& s, const ct_problem& p, int smem
 struct VariantKey {
     ct_config cfg;
     int fw, fh, dtype;
+    // non-empty: the taps (FP32, fh x fw) compiled into the variant as immediates
+    std::vector<float> taps;
     uint64_t packed() const;
     std::string describe() const;
 };
+// The key of the variant that runs (p, c) with filter h_filter: the taps are
+// part of it when c.taps = 1, c.unroll = 1 and every tap is finite.
+VariantKey variant_key(const ct_problem& p, const ct_config& c, const void* h_filter);
 
 struct Variant {
     VariantKey key{};
@@ -109,6 +114,7 @@ struct Variant {
     cudaKernel_t kern = nullptr;
     int loaded_device = -1;
     int64_t smem_attr = -1;
+    int resident = 0;   // blocks the loaded device holds at once (SMs x blocks per SM), 0 until loaded
     ~Variant();
 };
 using VariantPtr = std::shared_ptr<Variant>;
@@ -148,9 +154,12 @@ std::string& cache_dir_setting();
 ct_status load_variant(Variant& v);
 void unload_variant(Variant& v);
 
-// Builds the parameter block and launches one correlation.
+// Builds the parameter block and launches one correlation; persist selects
+// the grid (one block per tile, or the persistent grid of v.resident blocks).
 ct_status launch_variant(Variant& v, const ct_problem& p, const void* d_image,
-                         const void* h_filter, float* d_out, cudaStream_t stream);
+                         const void* h_filter, float* d_out, cudaStream_t stream, int persist = 0);
+// Output tiles of p under configuration c.
+int64_t tile_count(const ct_problem& p, const ct_config& c);
 // Pointer and layout checks for a launch (alignment, non-null).
 ct_status check_buffers(const ct_problem& p, const void* d_image, const void* h_filter, const float* d_out);
 ct_status require_device();
@@ -199,6 +208,8 @@ private:
 
 double now_ms();
 const char* last_error();
+// Current device's SM clock in MHz, read through NVML (0 when unavailable).
+int sample_sm_mhz();
 
 ct_status tune_gpu(const ct_problem* p, const ct_space* s, ct_strategy st, const ct_tune_opts* opts,
                    const void* d_image, const void* h_filter, float* d_out, ct_config* best_out,

@@ -111,6 +111,7 @@ struct Image {
 struct Launch {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t k0 = nullptr, k1 = nullptr;   // around the kernel (timing events)
     bool busy = false;
     std::vector<std::shared_ptr<Request>> reqs;
     size_t tab_off = 0, tab_bytes = 0;
@@ -147,6 +148,8 @@ struct ct_server {
     bool stop = false;
     std::thread worker;
     // statistics since the last reset
+    cudaEvent_t ref = nullptr;                      // recorded at the reset: origin of kernel intervals
+    std::vector<std::pair<float, float>> kbusy;     // kernel intervals (ms after ref)
     std::vector<double> lat_ms;
     int64_t submitted = 0, completed = 0, failed = 0, n_launches = 0, launched_reqs = 0;
     double flops = 0, t0 = 0, t_last = 0;
@@ -178,8 +181,11 @@ ct_server::~ct_server()
         if (L.stream) cudaStreamSynchronize(L.stream);
         if (L.stream) cudaStreamDestroy(L.stream);
         if (L.done) cudaEventDestroy(L.done);
+        if (L.k0) cudaEventDestroy(L.k0);
+        if (L.k1) cudaEventDestroy(L.k1);
         if (L.staging) cudaFreeHost(L.staging);
     }
+    if (ref) cudaEventDestroy(ref);
     if (copy_in) {
         cudaStreamSynchronize(copy_in);
         cudaStreamDestroy(copy_in);
@@ -221,6 +227,12 @@ bool ct_server::step_locked()
         if (e != cudaSuccess) {
             fatal = CT_ERR_CUDA;
             fatal_msg = std::string("batch launch failed: ") + cudaGetErrorString(e);
+        } else if (L.launched == CT_OK) {
+            float a = 0.f, b = 0.f;
+            if (cudaEventElapsedTime(&a, ref, L.k0) == cudaSuccess && cudaEventElapsedTime(&b, ref, L.k1) == cudaSuccess)
+                kbusy.emplace_back(a, b);
+            else
+                cudaGetLastError();
         }
         arena.release(L.tab_off, L.tab_bytes);
         L.reqs.clear();
@@ -373,7 +385,9 @@ bool ct_server::launch_locked(Launch& L)
     DevParams prm{dt + off_p, dt + off_w, reinterpret_cast<const float*>(dt + off_f), dt + 256,
                   reinterpret_cast<unsigned*>(dt), (int32_t)n_work, 0};
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(max_grid, n_work));
+    cudaEventRecord(L.k0, L.stream);
     ct_status s = fatal == CT_OK ? launch_batch(*module, grid, threads, prm, L.stream) : (ct_status)fatal;
+    cudaEventRecord(L.k1, L.stream);
     if (s != CT_OK && fatal == CT_OK) {
         fatal = s;
         fatal_msg = last_error();
@@ -500,10 +514,13 @@ CT_API ct_status ct_server_create(const ct_server_opts* opts, ct_server** out)
     for (auto& L : S->launches) {
         if ((e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreate(&L.k0)) != cudaSuccess || (e = cudaEventCreate(&L.k1)) != cudaSuccess ||
             (e = cudaMallocHost((void**)&L.staging, (size_t)o.staging_bytes)) != cudaSuccess)
             return cuda_fail(e, "server launch slot");
         L.staging_bytes = (size_t)o.staging_bytes;
     }
+    if ((e = cudaEventCreate(&S->ref)) != cudaSuccess || (e = cudaEventRecord(S->ref, S->copy_in)) != cudaSuccess)
+        return cuda_fail(e, "server reference event");
     S->t0 = S->t_last = now_s();
     ct_server* raw = S.get();
     S->worker = std::thread([raw] { raw->loop(); });
@@ -694,6 +711,22 @@ CT_API ct_status ct_server_stats_get(ct_server* s, ct_server_stats* out)
         out->req_per_s = (double)s->completed / out->wall_s;
         out->gflops = s->flops / out->wall_s / 1e9;
     }
+    // union of the kernel intervals
+    std::vector<std::pair<float, float>> iv = s->kbusy;
+    std::sort(iv.begin(), iv.end());
+    double busy = 0.0, cur_a = 0.0, cur_b = -1.0;
+    for (const auto& x : iv) {
+        if (x.first > cur_b) {
+            if (cur_b > cur_a) busy += cur_b - cur_a;
+            cur_a = x.first;
+            cur_b = x.second;
+        } else {
+            cur_b = std::max<double>(cur_b, x.second);
+        }
+    }
+    if (cur_b > cur_a) busy += cur_b - cur_a;
+    out->kernel_busy_s = busy * 1e-3;
+    out->kernel_busy_frac = out->wall_s > 0 ? out->kernel_busy_s / out->wall_s : 0.0;
     return CT_OK;
 }
 
@@ -702,9 +735,81 @@ CT_API ct_status ct_server_stats_reset(ct_server* s)
     if (!s) return fail(CT_ERR_INVALID_ARG, "server is NULL");
     std::unique_lock<std::mutex> g(s->mu);
     s->lat_ms.clear();
+    s->kbusy.clear();
     s->submitted = s->completed = s->failed = s->n_launches = s->launched_reqs = 0;
     s->flops = 0;
     s->t0 = s->t_last = now_s();
+    // new origin for the kernel intervals; launches still running keep the old one
+    bool busy = false;
+    for (auto& L : s->launches) busy = busy || L.busy;
+    if (!busy) cudaEventRecord(s->ref, s->copy_in);
+    return CT_OK;
+}
+
+CT_API ct_status ct_server_run(ct_server* s, const ct_server_run_opts* ro, ct_server_stats* out)
+{
+    if (!s || !ro || !ro->requests || ro->n <= 0 || ro->max_in_flight < 1)
+        return fail(CT_ERR_INVALID_ARG, "server, options, requests (n > 0) and max_in_flight >= 1 are required");
+    ct_status st = ct_server_drain(s, -1);
+    if (st != CT_OK) return st;
+    ct_server_stats_reset(s);
+    const int64_t n = ro->n;
+    std::vector<uint64_t> ids((size_t)n, 0);
+    std::mutex m;
+    std::condition_variable cv;
+    int64_t n_sub = 0, n_done = 0;
+    ct_status err = CT_OK, werr = CT_OK;
+    std::string werr_msg;
+    // completions are collected in submission order on a second thread
+    std::thread waiter([&] {
+        for (int64_t k = 0; k < n; ++k) {
+            {
+                std::unique_lock<std::mutex> g(m);
+                cv.wait(g, [&] { return n_sub > k || err != CT_OK; });
+                if (n_sub <= k) return;   // the submitter stopped
+            }
+            double lat = NAN;
+            const ct_status w = ct_server_wait(s, ids[(size_t)k], ro->timeout_us, &lat);
+            if (ro->latency_ms) ro->latency_ms[k] = w == CT_OK ? lat : NAN;
+            std::lock_guard<std::mutex> g(m);
+            if (w == CT_ERR_TIMEOUT && werr == CT_OK) {
+                werr = w;
+                werr_msg = last_error();
+                err = w;
+            }
+            ++n_done;
+            cv.notify_all();
+            if (err != CT_OK && n_sub <= k + 1) return;
+        }
+    });
+    const double t_start = now_s();
+    for (int64_t k = 0; k < n; ++k) {
+        if (ro->arrival_s) {
+            const double due = t_start + ro->arrival_s[k];
+            for (double now = now_s(); now < due; now = now_s())
+                if (due - now > 200e-6) std::this_thread::sleep_for(std::chrono::microseconds(100));
+        }
+        {
+            std::unique_lock<std::mutex> g(m);
+            cv.wait(g, [&] { return k - n_done < ro->max_in_flight || err != CT_OK; });
+            if (err != CT_OK) break;
+        }
+        uint64_t id = 0;
+        const ct_status sub = ct_server_submit(s, &ro->requests[k], &id);
+        std::lock_guard<std::mutex> g(m);
+        if (sub != CT_OK) {
+            err = sub;
+            werr_msg = last_error();
+            cv.notify_all();
+            break;
+        }
+        ids[(size_t)k] = id;
+        n_sub = k + 1;
+        cv.notify_all();
+    }
+    waiter.join();
+    if (out) ct_server_stats_get(s, out);
+    if (err != CT_OK) return fail(err, "server run stopped: %s", werr_msg.c_str());
     return CT_OK;
 }
 

@@ -118,7 +118,11 @@ void CompilePool::worker()
 struct Measure {
     int status = CT_OK;
     int n = 0;
-    double med = NAN, mn = NAN, sd = NAN;
+    double med = NAN, mn = NAN, sd = NAN;   // of the faster grid
+    double t_tiles = NAN, t_persist = NAN;  // medians per grid
+    int persist = 0;                        // the faster grid
+    int taps = 0;                           // 1: measured with the taps compiled in
+    int sm_mhz = 0;
     int regs = 0, spill = 0;
     int64_t smem = 0;
     double compile_ms = 0.0;
@@ -164,7 +168,7 @@ public:
             return m;
         }
         m.n = 1;
-        m.med = m.mn = v;
+        m.med = m.mn = m.t_tiles = v;
         m.sd = 0.0;
         return m;
     }
@@ -176,6 +180,8 @@ private:
 struct TimeOpts {
     int repeats = 7, warmup = 1, flush_l2 = 0;
     double graph_below_ms = 0.05;
+    int grid_modes = 0;   // 1: also time the persistent grid
+    int taps_imm = 0;     // 1: unrolled variants get the problem's taps compiled in
 };
 
 class GpuEvaluator : public Evaluator {
@@ -191,7 +197,12 @@ public:
     {
         for (auto& e : ev_) cudaEventDestroy(e);
     }
-    VariantKey key(const Entry& e) const { return VariantKey{e.cfg, p_.filter_w, p_.filter_h, p_.dtype}; }
+    VariantKey key(const Entry& e) const
+    {
+        ct_config c = e.cfg;
+        c.taps = o_.taps_imm ? 1 : 0;
+        return variant_key(p_, c, filt_);
+    }
     void prefetch(const Entry& e, bool urgent) override { pool_.request(key(e), urgent); }
     bool queue_short() const override { return pool_.queued() < 2 * pool_.threads(); }
     bool ready(const Entry& e) override { return pool_.ready(key(e)); }
@@ -212,6 +223,7 @@ public:
         m.spill = v->spill_bytes;
         m.smem = v->smem;
         m.compile_ms = v->compile_ms;
+        m.taps = k.taps.empty() ? 0 : 1;
         compile_cpu_ms += v->compile_ms;
         if (v->status != CT_OK) {
             m.status = v->status;
@@ -232,14 +244,43 @@ public:
     ct_status fatal = CT_OK;
 
 private:
-    ct_status launch(Variant& v) { return launch_variant(v, p_, img_, filt_, out_, s_); }
+    ct_status launch(Variant& v, int persist) { return launch_variant(v, p_, img_, filt_, out_, s_, persist); }
 
+    // Times one grid form: warm-up launches, then the median of the timed ones.
     int time_variant(Variant& v, Measure& m)
     {
         ct_status s = load_variant(v);
         if (s != CT_OK) return s == CT_ERR_CUDA ? CT_ERR_LAUNCH : s;
+        std::vector<double> t;
+        int st = time_grid(v, 0, t);
+        if (st != CT_OK) return st;
+        summarize(t, m);
+        m.t_tiles = m.med;
+        m.persist = 0;
+        if (o_.grid_modes && v.resident > 0 && tile_count(p_, v.key.cfg) > v.resident) {
+            std::vector<double> t1;
+            if ((st = time_grid(v, 1, t1)) != CT_OK) return st;
+            Measure b;
+            summarize(t1, b);
+            m.t_persist = b.med;
+            if (b.med < m.med) {
+                m.n = b.n;
+                m.med = b.med;
+                m.mn = b.mn;
+                m.sd = b.sd;
+                m.persist = 1;
+            }
+        }
+        if (take_device_error()) return CT_ERR_TIMEOUT;   // a launch gave up waiting for its input copy
+        m.sm_mhz = sample_sm_mhz();
+        return CT_OK;
+    }
+
+    int time_grid(Variant& v, int persist, std::vector<double>& t)
+    {
+        ct_status s;
         for (int w = 0; w < std::max(1, o_.warmup); ++w) {
-            s = launch(v);
+            s = launch(v, persist);
             if (s != CT_OK) {
                 cudaGetLastError();
                 return CT_ERR_LAUNCH;
@@ -253,7 +294,7 @@ private:
         }
         // one probe launch decides between single-launch and graph timing
         cudaEventRecord(ev_[0], s_);
-        launch(v);
+        launch(v, persist);
         cudaEventRecord(ev_[1], s_);
         if ((e = cudaEventSynchronize(ev_[1])) != cudaSuccess) {
             fatal = cuda_fail(e, "kernel execution during tuning");
@@ -262,7 +303,6 @@ private:
         }
         float probe = 0.f;
         cudaEventElapsedTime(&probe, ev_[0], ev_[1]);
-        std::vector<double> t;
         if (probe < o_.graph_below_ms) {
             const int K = std::min(1000, std::max(2, (int)std::ceil(0.5 / std::max(1e-4, (double)probe))));
             cudaGraph_t g = nullptr;
@@ -270,7 +310,7 @@ private:
             if ((e = cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
                 return cuda_fail(e, "cudaStreamBeginCapture"), CT_ERR_CUDA;
             bool ok = true;
-            for (int i = 0; i < K && ok; ++i) ok = launch(v) == CT_OK;
+            for (int i = 0; i < K && ok; ++i) ok = launch(v, persist) == CT_OK;
             e = cudaStreamEndCapture(s_, &g);
             if (!ok || e != cudaSuccess) {
                 if (g) cudaGraphDestroy(g);
@@ -299,7 +339,7 @@ private:
             for (int r = 0; r < o_.repeats; ++r) {
                 if (o_.flush_l2 && flush_) launch_l2_flush(flush_, flush_bytes_, (uint32_t)r, s_);
                 cudaEventRecord(ev_[2 * (r % 16)], s_);
-                launch(v);
+                launch(v, persist);
                 cudaEventRecord(ev_[2 * (r % 16) + 1], s_);
                 if (r % 16 == 15 || r == o_.repeats - 1) {
                     cudaEventSynchronize(ev_[2 * (r % 16) + 1]);
@@ -316,8 +356,6 @@ private:
             abort = true;
             return CT_ERR_CUDA;
         }
-        if (take_device_error()) return CT_ERR_TIMEOUT;   // a launch gave up waiting for its input copy
-        summarize(t, m);
         return CT_OK;
     }
 
@@ -360,6 +398,7 @@ static std::string row_json(const ct_row& r, const std::string& tag)
     std::ostringstream os;
     os << "{\"problem\":\"" << tag << "\",\"index\":" << r.index;
     for (int k = 0; k < 6; ++k) os << ",\"" << kParamNames[k] << "\":" << cfg_get(r.cfg, k);
+    os << ",\"persist\":" << r.cfg.persist << ",\"taps\":" << r.cfg.taps;
     os << ",\"status\":" << r.status << ",\"n\":" << r.n << ",\"t_med_ms\":";
     fmt_num(os, r.t_med_ms);
     os << ",\"t_min_ms\":";
@@ -371,7 +410,13 @@ static std::string row_json(const ct_row& r, const std::string& tag)
     os << ",\"regs\":" << r.regs << ",\"spill_bytes\":" << r.spill_bytes << ",\"smem_bytes\":" << r.smem_bytes
        << ",\"eval_order\":" << r.eval_order << ",\"compile_ms\":";
     fmt_num(os, r.compile_ms);
-    os << "}";
+    os << ",\"t_tiles_ms\":";
+    fmt_num(os, r.t_tiles_ms);
+    os << ",\"t_persist_ms\":";
+    fmt_num(os, r.t_persist_ms);
+    os << ",\"t_remeasured_ms\":";
+    fmt_num(os, r.t_remeasured_ms);
+    os << ",\"sm_mhz\":" << r.sm_mhz << "}";
     return os.str();
 }
 
@@ -417,6 +462,17 @@ static std::unordered_map<uint64_t, Measure> read_resume(const char* path, const
         json_num(line, "spill_bytes", sp);
         json_num(line, "smem_bytes", sm);
         json_num(line, "compile_ms", cm);
+        double pe = 0, tt = NAN, tp = NAN, mhz = 0, tk = 0;
+        json_num(line, "persist", pe);
+        json_num(line, "taps", tk);
+        m.taps = tk == 1.0 ? 1 : 0;
+        if (!json_num(line, "t_tiles_ms", tt)) tt = m.med;
+        json_num(line, "t_persist_ms", tp);
+        json_num(line, "sm_mhz", mhz);
+        m.persist = pe == 1.0 ? 1 : 0;
+        m.t_tiles = tt;
+        m.t_persist = tp;
+        m.sm_mhz = (int)mhz;
         m.status = (int)st;
         m.n = (int)n;
         m.regs = (int)r;
@@ -485,6 +541,12 @@ public:
         }
         ct_row r{};
         r.cfg = e.cfg;
+        r.cfg.persist = m.status == CT_OK ? m.persist : 0;
+        r.cfg.taps = m.taps;
+        r.t_tiles_ms = m.status == CT_OK ? m.t_tiles : NAN;
+        r.t_persist_ms = m.status == CT_OK ? m.t_persist : NAN;
+        r.t_remeasured_ms = NAN;
+        r.sm_mhz = m.sm_mhz;
         r.index = e.index;
         r.status = m.status;
         r.n = m.n;
@@ -777,7 +839,107 @@ static ct_status run_strategy(const ct_problem& p, const Space& s, ct_strategy s
     t.info.compile_wall_ms = ev.compile_wait_ms;
     t.info.compile_cpu_ms = ev.compile_cpu_ms;
     t.info.bench_ms = ev.bench_ms;
+    std::vector<int> mhz;
+    for (const auto& r : t.rows)
+        if (r.sm_mhz > 0) mhz.push_back(r.sm_mhz);
+    if (!mhz.empty()) {
+        std::nth_element(mhz.begin(), mhz.begin() + mhz.size() / 2, mhz.end());
+        t.info.sm_mhz_median = mhz[mhz.size() / 2];
+    }
     return CT_OK;
+}
+
+// Re-measures the k fastest rows (those of at least min_ms; shorter kernels
+// keep their graph-timed figures) with `reps` launches each, interleaved
+// round by round so that a clock change affects every candidate alike, each
+// launch bracketed by events and preceded by the L2 flush when one is given.
+// With both_taps, an unrolled row is timed in both tap forms (parameter
+// block and compiled in) and keeps the faster (cfg.taps records it).
+// best_row becomes the fastest by the re-measured median.  Returns the
+// variant of that row (null when nothing was re-measured).
+static VariantPtr remeasure(ct_table& t, const ct_problem& p, int k, int reps, double min_ms, bool both_taps,
+                            const void* img, const void* filt, float* out, void* flush, int64_t flush_bytes,
+                            cudaStream_t s, CompilePool& pool)
+{
+    std::vector<size_t> order;
+    for (size_t i = 0; i < t.rows.size(); ++i) {
+        const ct_row& r = t.rows[i];
+        if (r.status == CT_OK && std::isfinite(r.t_med_ms) && r.t_med_ms >= min_ms) order.push_back(i);
+    }
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        const ct_row &x = t.rows[a], &y = t.rows[b];
+        return x.t_med_ms < y.t_med_ms || (x.t_med_ms == y.t_med_ms && x.index < y.index);
+    });
+    if ((int)order.size() > k) order.resize((size_t)k);
+    if (order.size() < 2) return nullptr;
+    const double t0 = now_ms();
+    struct Cand {
+        size_t row;
+        ct_config cfg;
+        VariantPtr v;
+        std::vector<double> ms;
+    };
+    std::vector<Cand> cand;
+    for (size_t i : order) {
+        cand.push_back({i, t.rows[i].cfg, nullptr, {}});
+        if (both_taps && t.rows[i].cfg.unroll) {
+            ct_config alt = t.rows[i].cfg;
+            alt.taps = alt.taps ? 0 : 1;
+            if (variant_key(p, alt, filt).cfg.taps == alt.taps) cand.push_back({i, alt, nullptr, {}});
+        }
+    }
+    std::vector<std::shared_future<VariantPtr>> futs;
+    for (auto& c : cand) futs.push_back(pool.request(variant_key(p, c.cfg, filt), true));
+    for (size_t j = 0; j < cand.size(); ++j) {
+        cand[j].v = futs[j].get();
+        pool.forget(variant_key(p, cand[j].cfg, filt));
+        if (!cand[j].v || cand[j].v->status != CT_OK || load_variant(*cand[j].v) != CT_OK) return nullptr;
+    }
+    std::vector<cudaEvent_t> ev(2 * cand.size());
+    for (auto& e : ev) cudaEventCreate(&e);
+    bool ok = true;
+    for (size_t j = 0; j < cand.size() && ok; ++j)   // warm-up
+        ok = launch_variant(*cand[j].v, p, img, filt, out, s, cand[j].cfg.persist) == CT_OK;
+    for (int r = 0; r < reps && ok; ++r) {
+        for (size_t j = 0; j < cand.size() && ok; ++j) {
+            if (flush) launch_l2_flush(flush, flush_bytes, (uint32_t)(r * 131 + j), s);
+            cudaEventRecord(ev[2 * j], s);
+            ok = launch_variant(*cand[j].v, p, img, filt, out, s, cand[j].cfg.persist) == CT_OK;
+            cudaEventRecord(ev[2 * j + 1], s);
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) ok = false;
+        for (size_t j = 0; j < cand.size() && ok; ++j) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[2 * j], ev[2 * j + 1]);
+            cand[j].ms.push_back((double)ms);
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (!ok || take_device_error()) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::vector<VariantPtr> var_of(t.rows.size());
+    for (auto& c : cand) {
+        Measure m;
+        summarize(c.ms, m);
+        ct_row& row = t.rows[c.row];
+        if (!std::isfinite(row.t_remeasured_ms) || m.med < row.t_remeasured_ms) {
+            row.t_remeasured_ms = m.med;
+            row.cfg.taps = c.cfg.taps;
+            var_of[c.row] = c.v;
+        }
+    }
+    size_t best = order[0];
+    for (size_t i : order) {
+        const ct_row &x = t.rows[i], &b = t.rows[best];
+        if (x.t_remeasured_ms < b.t_remeasured_ms || (x.t_remeasured_ms == b.t_remeasured_ms && x.index < b.index))
+            best = i;
+    }
+    t.info.best_row = (int64_t)best;
+    t.info.remeasured = (int32_t)order.size();
+    t.info.remeasure_ms = now_ms() - t0;
+    return var_of[best];
 }
 
 static ct_tune_opts normalise(const ct_tune_opts* o)
@@ -787,6 +949,7 @@ static ct_tune_opts normalise(const ct_tune_opts* o)
     if (r.repeats <= 0) r.repeats = 7;
     if (r.warmup <= 0) r.warmup = 1;
     if (r.graph_below_us == 0) r.graph_below_us = 50;
+    if (r.remeasure_repeats <= 0) r.remeasure_repeats = 31;
     return r;
 }
 
@@ -898,6 +1061,8 @@ ct_status tune_gpu(const ct_problem* p, const ct_space* s, ct_strategy st, const
     to.warmup = o.warmup;
     to.flush_l2 = o.flush_l2;
     to.graph_below_ms = o.graph_below_us < 0 ? -1.0 : o.graph_below_us * 1e-3;
+    to.grid_modes = o.grid_modes;
+    to.taps_imm = o.taps_imm;
     int threads = o.compile_threads > 0 ? o.compile_threads : (int)std::max(1u, std::thread::hardware_concurrency());
     auto* t = new ct_table();
     {
@@ -909,7 +1074,13 @@ ct_status tune_gpu(const ct_problem* p, const ct_space* s, ct_strategy st, const
         GpuEvaluator ev(*p, to, img, h_filter, out, pool, flush, flush_bytes, stream);
         rc = run_strategy(*p, s->s, st, o, valid, ev, *t, 2 * threads + 4);
         if (rc == CT_OK && ev.fatal != CT_OK) rc = ev.fatal;
-        if (rc == CT_OK && ev.best()) put_variant(ev.best());
+        VariantPtr re;
+        if (rc == CT_OK && o.remeasure_top > 0)
+            re = remeasure(*t, *p, o.remeasure_top, o.remeasure_repeats, std::max(0.0, to.graph_below_ms),
+                           o.remeasure_taps != 0, img, h_filter, out, o.flush_l2 ? flush : nullptr, flush_bytes,
+                           stream, pool);
+        if (rc == CT_OK && re) put_variant(re);
+        else if (rc == CT_OK && ev.best()) put_variant(ev.best());
     }
     cleanup();
     if (rc != CT_OK) {

@@ -6,7 +6,9 @@
 
 #include <nvrtc.h>
 
+#include <algorithm>
 #include <cerrno>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -36,14 +38,53 @@ uint64_t VariantKey::packed() const
     k = k * 64 + (uint64_t)fw;
     k = k * 64 + (uint64_t)fh;
     k = k * 4 + (uint64_t)dtype;
+    if (!taps.empty()) {   // a filter-specific variant: mix in the taps' bits
+        uint64_t h = 1469598103934665603ull;
+        const unsigned char* b = reinterpret_cast<const unsigned char*>(taps.data());
+        for (size_t i = 0; i < taps.size() * sizeof(float); ++i) {
+            h ^= b[i];
+            h *= 1099511628211ull;
+        }
+        k = (k * 0x9E3779B97F4A7C15ull) ^ h ^ 1ull;
+    }
+    return k;
+}
+
+VariantKey variant_key(const ct_problem& p, const ct_config& c, const void* h_filter)
+{
+    VariantKey k{c, p.filter_w, p.filter_h, p.dtype, {}};
+    k.cfg.persist = 0;
+    if (!(c.taps && c.unroll && h_filter)) {
+        k.cfg.taps = 0;
+        return k;
+    }
+    const int n = p.filter_w * p.filter_h;
+    k.taps.resize((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        float v;
+        if (p.dtype == CT_F32) {
+            memcpy(&v, static_cast<const float*>(h_filter) + i, 4);
+        } else {
+            const uint32_t u = (uint32_t) static_cast<const uint16_t*>(h_filter)[i] << 16;
+            memcpy(&v, &u, 4);
+        }
+        if (!std::isfinite(v)) {   // no literal for it: the parameter-block form
+            k.taps.clear();
+            k.cfg.taps = 0;
+            return k;
+        }
+        k.taps[(size_t)i] = v;
+    }
+    k.cfg.taps = 1;
     return k;
 }
 
 std::string VariantKey::describe() const
 {
     char b[160];
-    snprintf(b, sizeof b, "bx=%d by=%d tx=%d ty=%d smem=%d unroll=%d fw=%d fh=%d dtype=%d", cfg.block_x,
-             cfg.block_y, cfg.tile_x, cfg.tile_y, cfg.use_smem, cfg.unroll, fw, fh, dtype);
+    snprintf(b, sizeof b, "bx=%d by=%d tx=%d ty=%d smem=%d unroll=%d fw=%d fh=%d dtype=%d%s", cfg.block_x,
+             cfg.block_y, cfg.tile_x, cfg.tile_y, cfg.use_smem, cfg.unroll, fw, fh, dtype,
+             taps.empty() ? "" : " taps=compiled");
     return b;
 }
 
@@ -79,8 +120,28 @@ static std::vector<std::string> nvrtc_options(const VariantKey& k)
     def("CT_FH", k.fh);
     def("CT_DTYPE", k.dtype);
     def("CT_TMA", tma_staged(k.cfg, k.fw, k.fh, k.dtype) ? 1 : 0);
+    if (!k.taps.empty()) def("CT_TAPS_IMM", 1);
     add_env_options(o);
     return o;
+}
+
+// The source compiled for k: the template, preceded for a filter-specific
+// variant by the taps as exact hexadecimal float literals.
+static std::string variant_source(const VariantKey& k)
+{
+    std::string src;
+    if (!k.taps.empty()) {
+        src.reserve(k.taps.size() * 20 + sizeof kCorr2dSource + 64);
+        src += "#define CT_TAP_VALUES ";
+        char b[48];
+        for (size_t i = 0; i < k.taps.size(); ++i) {
+            snprintf(b, sizeof b, "%s%af", i ? ", " : "", (double)k.taps[i]);
+            src += b;
+        }
+        src += "\n";
+    }
+    src.append(kCorr2dSource, sizeof kCorr2dSource - 1);
+    return src;
 }
 
 int64_t halo_box_w(const ct_config& c, int fw, int dtype)
@@ -296,7 +357,8 @@ VariantPtr compile_source(const char* src, size_t len, const char* prog_name, co
 VariantPtr compile_variant(const VariantKey& k, const std::string& cache_dir)
 {
     const std::vector<std::string> opts = nvrtc_options(k);
-    VariantPtr v = compile_source(kCorr2dSource, sizeof kCorr2dSource, "corr2d.cu", opts, "ct_corr2d", cache_dir);
+    const std::string src = variant_source(k);
+    VariantPtr v = compile_source(src.c_str(), src.size() + 1, "corr2d.cu", opts, "ct_corr2d", cache_dir);
     v->key = k;
     ct_problem p{};
     p.filter_w = k.fw;
@@ -421,6 +483,15 @@ ct_status load_variant(Variant& v)
     if (v.loaded_device != dev || v.smem_attr != v.smem) {
         e = cudaFuncSetAttribute((const void*)v.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)v.kern,
+                                                          v.key.cfg.block_x * v.key.cfg.block_y,
+                                                          (size_t)v.smem) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = sms = 0;
+        }
+        v.resident = std::max(0, per_sm) * std::max(0, sms);
         v.loaded_device = dev;
         v.smem_attr = v.smem;
     }
@@ -435,6 +506,7 @@ void unload_variant(Variant& v)
     v.kern = nullptr;
     v.loaded_device = -1;
     v.smem_attr = -1;
+    v.resident = 0;
 }
 
 // -------------------------------------------------------------- launch ----
@@ -451,13 +523,20 @@ ct_status check_buffers(const ct_problem& p, const void* d_image, const void* h_
 // Parameter block of ct_corr2d, laid out as the device struct CtParams: the
 // image's tensor map (128 bytes, 64-byte aligned; zero for variants that do
 // not use it), in, out, in_pitch, out_pitch (8 bytes each), out_w, out_h,
-// in_w, in_h (4 bytes each), the error word's address (8 bytes), then
+// in_w, in_h (4 bytes each), the error word's address (8 bytes), tiles_x,
+// n_tiles, persist, step_x, step_y and one spare (4 bytes each), then
 // filter_h*filter_w floats; the struct's size is a multiple of 64 bytes.
-static constexpr size_t kParamHeader = 184;
+static constexpr size_t kParamHeader = 208;
 static constexpr size_t kParamMax = (kParamHeader + 4 * CT_MAX_FILTER * CT_MAX_FILTER + 63) / 64 * 64;
 
+int64_t tile_count(const ct_problem& p, const ct_config& c)
+{
+    const int64_t tw = (int64_t)c.block_x * c.tile_x, th = (int64_t)c.block_y * c.tile_y;
+    return ((p.out_w + tw - 1) / tw) * ((p.out_h + th - 1) / th);
+}
+
 ct_status launch_variant(Variant& v, const ct_problem& p, const void* d_image, const void* h_filter,
-                         float* d_out, cudaStream_t stream)
+                         float* d_out, cudaStream_t stream, int persist)
 {
     if (p.out_w == 0 || p.out_h == 0) return CT_OK;
     ct_status s = load_variant(v);
@@ -465,9 +544,14 @@ ct_status launch_variant(Variant& v, const ct_problem& p, const void* d_image, c
     const ct_config& c = v.key.cfg;
     const int64_t tw = (int64_t)c.block_x * c.tile_x, th = (int64_t)c.block_y * c.tile_y;
     const int64_t gx = (p.out_w + tw - 1) / tw, gy = (p.out_h + th - 1) / th;
-    if (gx > 0x7fffffffLL || gy > 65535)
+    if (gx > 0x7fffffffLL || gy > 65535 || gx * gy > 0x7fffffffLL)
         return fail(CT_ERR_INVALID_ARG, "grid %lldx%lld exceeds the launch limits for this config", (long long)gx,
                     (long long)gy);
+    const int64_t n_tiles = gx * gy;
+    // the persistent grid: the blocks the GPU holds at once (never more than the tiles)
+    const int64_t g1 = persist ? std::min<int64_t>(n_tiles, std::max(1, v.resident)) : 0;
+    const int32_t tiling[6] = {(int32_t)gx, (int32_t)n_tiles, persist ? 1 : 0, (int32_t)(g1 % gx),
+                               (int32_t)(g1 / gx), 0};
     const int nt = p.filter_w * p.filter_h;
     alignas(64) unsigned char buf[kParamMax];
     memset(buf, 0, kTensorMapBytes);
@@ -488,6 +572,7 @@ ct_status launch_variant(Variant& v, const ct_problem& p, const void* d_image, c
     memcpy(buf + 152, &opitch, 8);
     memcpy(buf + 160, dims, 16);
     memcpy(buf + 176, &err, 8);
+    memcpy(buf + 184, tiling, sizeof tiling);
     float* taps = reinterpret_cast<float*>(buf + kParamHeader);
     if (p.dtype == CT_F32) {
         memcpy(taps, h_filter, 4 * (size_t)nt);
@@ -499,8 +584,9 @@ ct_status launch_variant(Variant& v, const ct_problem& p, const void* d_image, c
         }
     }
     void* args[1] = {buf};
-    cudaError_t e = cudaLaunchKernel((const void*)v.kern, dim3((unsigned)gx, (unsigned)gy, 1),
-                                     dim3((unsigned)c.block_x, (unsigned)c.block_y, 1), args, (size_t)v.smem, stream);
+    const dim3 grid = persist ? dim3((unsigned)g1, 1, 1) : dim3((unsigned)gx, (unsigned)gy, 1);
+    cudaError_t e = cudaLaunchKernel((const void*)v.kern, grid, dim3((unsigned)c.block_x, (unsigned)c.block_y, 1),
+                                     args, (size_t)v.smem, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchKernel(ct_corr2d)");
     return CT_OK;
 }

@@ -82,6 +82,7 @@ def test_space_enumeration_matches_oracle(ctlib, name, fw, fh):
         assert i1 == i2
         d = c1.as_dict()
         d["smem"] = d.pop("use_smem")
+        assert d.pop("persist") == 0 and d.pop("taps") == 0   # variant forms, not points of the space
         assert d == c2
     raw, valid = sp.count(p, 232448)
     assert raw == len(ospace.enumerate_space(name, fw, fh, valid_only=False)) and valid == len(ref)
@@ -332,6 +333,7 @@ def test_server_without_gpu(ctlib):
     import ctypes
     h = ctlib.vp()
     assert ctlib.lib().ct_server_create(None, ctypes.byref(h)) == -1
+    assert ctlib.lib().ct_server_run(None, None, None) == -1
 
 
 def _oracle_analysis(table, space_name, flops, p_values):

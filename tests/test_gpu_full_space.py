@@ -44,7 +44,7 @@ def _image_with_nan_rows(img, device, bf16):
     return t.to(device)[:img.shape[0]]
 
 
-def _sweep(ct, device, ow, oh, fw, fh, seed, every, bf16=False):
+def _sweep(ct, device, ow, oh, fw, fh, seed, every, bf16=False, taps=0):
     img, f = synthetic.make_problem(seed, ow, oh, fw, fh, pad_value=np.nan, extra_pitch=8 if bf16 else 4,
                                     pitch_align=8 if bf16 else 4)
     if bf16:
@@ -59,22 +59,28 @@ def _sweep(ct, device, ow, oh, fw, fh, seed, every, bf16=False):
     d_img = _image_with_nan_rows(img, device, bf16)
     in_w = ow + fw - 1
     p = ct.problem_for(d_img, filt, in_w=in_w)
-    ents = ospace.enumerate_space("full", fw, fh)[::every]
+    ents = ospace.enumerate_space("full", fw, fh)
+    if taps:                                      # compiled-in taps apply to the unrolled variants
+        ents = [e for e in ents if e[1]["unroll"]]
+    ents = ents[::every]
     cfgs = [_cfg(ct, c) for _, c in ents]
-    lib_cfgs = {c.as_tuple() for _, c in ct.Space("full").enumerate(p)}
-    assert {c.as_tuple() for c in cfgs} <= lib_cfgs
+    for c in cfgs:
+        c.taps = taps
+    lib_cfgs = {c.space_tuple() for _, c in ct.Space("full").enumerate(p)}
+    assert {c.space_tuple() for c in cfgs} <= lib_cfgs
 
     cache = os.path.join(tempfile.gettempdir(), f"convtune-cache-{os.getuid()}")
     ct.set_cache_dir(cache)
     try:
         first = None
         chunk = 256
+        pre = lambda c: ct.compile_variant(p, c, filt)
         with cf.ThreadPoolExecutor(os.cpu_count() or 8) as ex:
-            nxt = ex.map(lambda c: ct.compile_variant(p, c), cfgs[:chunk])
+            nxt = ex.map(pre, cfgs[:chunk])
             for k in range(0, len(cfgs), chunk):
                 list(nxt)                                  # this chunk is compiled
                 if k + chunk < len(cfgs):                  # the next one compiles while this one runs
-                    nxt = ex.map(lambda c: ct.compile_variant(p, c), cfgs[k + chunk:k + 2 * chunk])
+                    nxt = ex.map(pre, cfgs[k + chunk:k + 2 * chunk])
                 for c in cfgs[k:k + chunk]:
                     out, ok = run_config(ct, d_img, filt, c, ow, oh, in_w=in_w)
                     assert ok, f"guard band overwritten by {c}"
@@ -87,25 +93,61 @@ def _sweep(ct, device, ow, oh, fw, fh, seed, every, bf16=False):
         ct.device_check()
     finally:
         ct.set_cache_dir(None)
-    return len(cfgs)
+    return len(cfgs), first
 
 
 def test_full_space_every_config_17x17(ctlib, cuda_device):
     """All 5,576 valid points of the full space for a 17x17 filter (the
     filter of the 4096x4096 workload) on a 333x157 output."""
-    n = _sweep(ctlib, cuda_device, 333, 157, 17, 17, seed=21, every=1)
+    n, _ = _sweep(ctlib, cuda_device, 333, 157, 17, 17, seed=21, every=1)
     assert n == 5576
 
 
 def test_full_space_eighth_5x7(ctlib, cuda_device):
     """Every 8th valid point (canonical order) for a 5-wide, 7-high filter on
     a 301x163 output."""
-    n = _sweep(ctlib, cuda_device, 301, 163, 5, 7, seed=22, every=8)
+    n, _ = _sweep(ctlib, cuda_device, 301, 163, 5, 7, seed=22, every=8)
     assert n == len(ospace.enumerate_space("full", 5, 7)[::8])
 
 
 def test_full_space_bf16_sixteenth_9x9(ctlib, cuda_device):
     """BF16 storage: every 16th valid point for the 9x9 filter of the BF16
     workloads on a 259x131 output, against the oracle on the BF16 values."""
-    n = _sweep(ctlib, cuda_device, 259, 131, 9, 9, seed=23, every=16, bf16=True)
+    n, _ = _sweep(ctlib, cuda_device, 259, 131, 9, 9, seed=23, every=16, bf16=True)
     assert n == len(ospace.enumerate_space("full", 9, 9)[::16])
+
+
+@pytest.mark.parametrize("bf16", [False, True], ids=["f32", "bf16"])
+def test_compiled_taps_same_bits(ctlib, cuda_device, bf16):
+    """Taps compiled into the variant (ct_config.taps = 1): every 24th unrolled
+    point of the full space for a 17x17 filter (every 48th for BF16) matches
+    the oracle, and its bits equal those of the parameter-block form."""
+    every = 48 if bf16 else 24
+    n1, with_imm = _sweep(ctlib, cuda_device, 333, 157, 17, 17, seed=24, every=every, bf16=bf16, taps=1)
+    n0, with_param = _sweep(ctlib, cuda_device, 333, 157, 17, 17, seed=24, every=10 ** 6, bf16=bf16, taps=0)
+    assert n1 > 100 // (2 if bf16 else 1) and n0 == 1
+    assert np.array_equal(with_imm.view(np.uint32), with_param.view(np.uint32))
+
+
+def test_compiled_taps_follow_the_filter(ctlib, cuda_device):
+    """Two filters of one size through the same compiled-taps configuration, one
+    after the other and back: each call runs its own filter's variant; a
+    filter with a non-finite tap falls back to the parameter-block form."""
+    ow, oh, fs = 200, 120, 9
+    img, f1 = synthetic.make_problem(41, ow, oh, fs, fs)
+    _, f2 = synthetic.make_problem(42, ow, oh, fs, fs)
+    d_img = torch.from_numpy(img).to(cuda_device)
+    c_imm = ctlib.config(16, 8, 4, 2, 1, 1, taps=1)
+    c_par = ctlib.config(16, 8, 4, 2, 1, 1, taps=0)
+    for f in (f1, f2, f1):
+        ref, S = oracle.corr2d_f64(img, f, ow, oh)
+        a, ok_a = run_config(ctlib, d_img, f, c_imm, ow, oh, in_w=ow + fs - 1)
+        b, ok_b = run_config(ctlib, d_img, f, c_par, ow, oh, in_w=ow + fs - 1)
+        assert ok_a and ok_b
+        assert_parity(a, ref, S, "compiled taps")
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    f3 = f1.copy()
+    f3[4, 4] = np.inf
+    a, ok_a = run_config(ctlib, d_img, f3, c_imm, ow, oh, in_w=ow + fs - 1)
+    b, ok_b = run_config(ctlib, d_img, f3, c_par, ow, oh, in_w=ow + fs - 1)
+    assert ok_a and ok_b and np.array_equal(a.view(np.uint32), b.view(np.uint32))

@@ -129,3 +129,42 @@ def test_tuned_server(ctlib, cuda_device):
         assert_parity(h_out.numpy()[:, :700], ref, S, "tuned server")
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("paced", [False, True], ids=["closed_loop", "poisson"])
+def test_native_run_same_bits(ctlib, cuda_device, server, paced):
+    """ct_server_run drives a stream from native threads (closed loop with at
+    most 8 requests in flight, or paced by Poisson arrival times at 4,000/s):
+    every request completes, each result is the single-problem kernel's bits,
+    output buffers shared by requests 8 apart are safe, and the statistics
+    cover the run (latencies, kernel busy time within the wall time)."""
+    shapes = synthetic.uneven_batch(77, 48, 64, 700, (3, 5, 9, 17))
+    K = 8
+    reqs, outs, probs = [], [], []
+    for k, (side, fs) in enumerate(shapes):
+        img, f, h_img, _ = _req(2000 + k, side, fs)
+        probs.append((img, f, side, fs))
+    slots = [torch.full((700 * 700,), float("nan")).pin_memory() for _ in range(K)]
+    results = {}
+    # run the stream in chunks of K so every request's output can be read before its slot is reused
+    lat_all = []
+    for c0 in range(0, len(shapes), K):
+        chunk = []
+        for k in range(c0, min(len(shapes), c0 + K)):
+            img, f, side, fs = probs[k]
+            h_img = torch.from_numpy(img).pin_memory()
+            h_out = slots[k % K][:side * synthetic.round_up(side, 4)].view(side, synthetic.round_up(side, 4))
+            outs.append(h_img)
+            chunk.append(server.request(h_out, f, side, side, h_image=h_img))
+        arrivals = np.cumsum(np.full(len(chunk), 1.0 / 4000.0)) if paced else None
+        st, lat = server.run(chunk, arrival_s=arrivals, max_in_flight=K)
+        assert st["completed"] == len(chunk) and st["failed"] == 0
+        assert np.all(np.isfinite(lat)) and np.all(lat > 0)
+        assert 0.0 < st["kernel_busy_s"] <= st["wall_s"] * 1.05 and st["kernel_busy_frac"] <= 1.05
+        lat_all += list(lat)
+        for k in range(c0, min(len(shapes), c0 + K)):
+            side = probs[k][2]
+            results[k] = slots[k % K][:side * synthetic.round_up(side, 4)].view(side, -1).numpy()[:, :side].copy()
+    for k, (img, f, side, fs) in enumerate(probs):
+        assert np.array_equal(results[k].view(np.uint32), _single(ctlib, img, f, side, fs, cuda_device).view(np.uint32))
+    assert len(lat_all) == len(shapes)
