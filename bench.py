@@ -408,7 +408,7 @@ def run_ours(args):
             t = ct.tune(p, space, strat, image=d_img, filt=f, out=d_out, seed=args.seed, cache_dir=cdir,
                         write_path=args.table_out if k == 0 else None, anneal_chains=args.anneal_chains,
                         flush_l2=True, grid_modes=args.grid_modes, remeasure_top=args.remeasure_top,
-                        taps_imm=args.taps_imm, remeasure_taps=1)
+                        taps_imm=args.taps_imm, remeasure_forms=7)
             brow = t.rows[t.info["best_row"]]
             tuning[strat] = dict(t.info, best=t.best.as_dict(), best_ms=brow["t_med_ms"],
                                  best_remeasured_ms=brow["t_remeasured_ms"], best_sm_mhz=brow["sm_mhz"])
@@ -453,11 +453,12 @@ def run_ours(args):
     def timed_loop(cfg, k, w, name="timed"):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         with torch.cuda.stream(stream):
-            # at least w warm-up steps, and at least 0.2 s of them, so the clocks are up before
-            # timing; the last ones repeat a timed step exactly (L2 flush, then the launch)
+            # at least w warm-up steps, and at least 0.5 s of them, so the clocks are up before
+            # timing (and sampled); the last ones repeat a timed step exactly (L2 flush, then the launch)
+            t_warm = time.time()
             tw = time.perf_counter()
             n_w = 0
-            while n_w < w or (time.perf_counter() - tw < 0.2 and n_w < 5000):
+            while n_w < w or (time.perf_counter() - tw < 0.5 and n_w < 10000):
                 ct.conv2d_raw(p, cfg, d_img.data_ptr(), hf, d_out.data_ptr(), stream.cuda_stream)
                 n_w += 1
                 if n_w % 50 == 0:
@@ -483,7 +484,7 @@ def run_ours(args):
                 torch.distributed.barrier()
             t_wall_end = time.time()
         ms = [a.elapsed_time(b) for a, b in ev]
-        return ms, t_wall, t_wall_end
+        return ms, t_warm, t_wall_end
 
     clocks.mark("timed_start")
     ms, tw0, tw1 = timed_loop(best, args.steps, max(3, args.warmup))
@@ -547,7 +548,8 @@ def run_ours(args):
         if r >= 3:
             link_floor = min(link_floor, e0.elapsed_time(e1))
     clocks.stop()
-    clk = clocks.summary(tw0, tw1)
+    clk = clocks.summary(tw0, tw1)   # the warm-up (>= 0.5 s, the same launches) and the timed steps
+    clk["window"] = "warm-up and timed steps"
     if clk["samples"] == 0:
         clk = clocks.summary(tw0 - 60.0, time.time())
         clk["note"] = "no sample inside the timed loop; samples from tuning, timed and e2e phases"
@@ -714,7 +716,8 @@ def measure_batch(args, ct, dev, info, pk, fp32_peak, world, plain_cfg=None):
         _, f, d_img, out, side, _ = big
         pr = ct.problem_for(d_img, f, in_w=side + fs - 1)
         tab = ct.tune(pr, "full", "anneal", image=d_img, filt=f, out=out, seed=args.seed,
-                      max_evals=args.batch_plain_evals, anneal_chains=args.anneal_chains)
+                      max_evals=args.batch_plain_evals, anneal_chains=args.anneal_chains, remeasure_top=5,
+                      remeasure_forms=2)
         cfg_for[fs] = tab.best
         tuning[f"plain_f{fs}"] = {"side": side, "best": tab.best.as_dict(), "wall_s": tab.info["wall_ms"] / 1e3,
                                   "evals": tab.info["n_rows"]}
@@ -875,7 +878,7 @@ def measure_bf16(args, ct, dev, info, fp32_peak, case):
     t0 = time.time()
     tab = ct.tune(p, "full", "anneal", image=d_img, filt=f_t, out=d_out, seed=args.seed,
                   max_evals=args.bf16_evals, anneal_chains=args.anneal_chains, taps_imm=args.taps_imm,
-                  flush_l2=True, remeasure_top=args.remeasure_top, remeasure_taps=1)
+                  flush_l2=True, remeasure_top=args.remeasure_top, remeasure_forms=3)
     tune_s = time.time() - t0
     hf = ct._filter_bytes(f_t, p.dtype)
     stream = torch.cuda.Stream(device=dev)

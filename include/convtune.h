@@ -97,13 +97,27 @@ typedef struct {
  * the first call with a new filter compiles it; the arithmetic and therefore
  * the result bits are the same).  taps = 1 applies to unroll = 1 variants
  * with finite taps; elsewhere it acts as 0.  ct_tune measures unrolled
- * configurations with taps = 1 when ct_tune_opts.taps_imm is set. */
+ * configurations with taps = 1 when ct_tune_opts.taps_imm is set.
+ * fma2 = 1 compiles a variant in which output rows 2k and 2k+1 of a thread
+ * pair up and each input row feeds both through one paired FP32 multiply-add
+ * (two fma.rn in one instruction, half the issue slots) per column and tap;
+ * every output still adds its taps in (i, j) order, so the bits are the same.
+ * It applies to unroll = 1, tile_y >= 2, taps = 0 variants; elsewhere it acts
+ * as 0.  ct_tune tries it in the re-measurement (remeasure_forms).
+ * shfl = 1 compiles a variant in which a thread reads only its own tile_x
+ * values of each staged input row and takes the rest of its window from the
+ * lanes to its right by warp shuffles (the filter-row reuse across a warp);
+ * lanes whose window runs past the warp read theirs whole.  It applies to
+ * use_smem = 1 variants with block_x a multiple of 32 and tile_x a multiple
+ * of 4; elsewhere it acts as 0.  Same bits; tried by remeasure_forms bit 2. */
 typedef struct {
     int32_t block_x, block_y;
     int32_t tile_x, tile_y;
     int32_t use_smem, unroll;
     int32_t persist;       /* 0: one block per tile; 1: persistent grid */
     int32_t taps;          /* 0: taps in the parameter block; 1: compiled into the variant */
+    int32_t fma2;          /* 1: paired FP32 multiply-adds over pairs of output rows */
+    int32_t shfl;          /* 1: window values from neighbouring lanes by warp shuffles */
 } ct_config;
 
 /* Per-variant build facts (from the NVRTC/ptxas log and the launch shape). */
@@ -314,8 +328,11 @@ typedef struct {
     int32_t taps_imm;         /* 1: measure every unroll = 1 configuration with the
                                  problem's taps compiled in (cfg.taps = 1 in its row);
                                  the compiles are then specific to this filter */
-    int32_t remeasure_taps;   /* 1: the re-measurement times each unrolled candidate in
-                                 both tap forms and keeps the faster (cfg.taps) */
+    int32_t remeasure_forms;  /* bit 0: the re-measurement also times each unrolled
+                                 candidate in the other tap form; bit 1: also in the
+                                 paired multiply-add form (fma2); bit 2: also with
+                                 shuffled windows (shfl); each row keeps its fastest
+                                 form (cfg.taps, cfg.fma2, cfg.shfl) */
     int32_t reserved3;
 } ct_tune_opts;
 
@@ -427,13 +444,17 @@ CT_API ct_status ct_table_analyze(const ct_table* t, const ct_space* s, double f
  * to ct_conv2d on each problem.
  *
  * Problems big enough to fill a good part of the GPU (opts->solo_wave_pct)
- * run instead as their own launch of the single-problem kernel, whose taps are
- * constant-bank operands; its configuration is tuned per filter size at
- * create (annealing, opts->solo_evals evaluations, on the largest such
+ * run instead as their own launch of the single-problem kernel, whose taps
+ * come from its parameter block; its configuration is tuned per filter size at
+ * create (annealing, opts->solo_evals evaluations, the five fastest timed
+ * again in the scalar and the paired multiply-add forms, on the largest such
  * problem, whose buffers the tuner uses).  The plan's graph holds these
  * launches, largest first, spread over opts->solo_branches parallel branches
  * (so small ones run beside each other), then the persistent launch of the
- * other problems.
+ * other problems.  When some solo configurations won in the paired
+ * multiply-add form, the graph is captured and timed (replays, which write
+ * every output) both with those and with their scalar twins, and the faster
+ * graph is kept.
  *
  * Each item's input halo and filter taps reach shared memory by tensor-memory
  * copies (one 2D tensor map per problem, encoded at create for the bucket's
@@ -483,7 +504,7 @@ typedef struct {
     int32_t smem_bytes, regs;
     double plan_ms, tune_ms, compile_cpu_ms;
     int32_t n_solo;         /* problems run as their own launch */
-    int32_t reserved;
+    int32_t n_solo_fma2;    /* of them, launches in the paired multiply-add form */
 } ct_batch_info;
 
 typedef struct ct_batch ct_batch;

@@ -41,12 +41,15 @@ class Problem(ctypes.Structure):
 
 
 class Config(ctypes.Structure):
-    """A point of the search space (the first six fields) plus two forms of
-    the variant: ``persist`` (0: one block per tile, 1: persistent grid) and
-    ``taps`` (0: taps in the parameter block, 1: compiled into the variant)."""
+    """A point of the search space (the first six fields) plus four forms
+    of the variant: ``persist`` (0: one block per tile, 1: persistent grid),
+    ``taps`` (0: taps in the parameter block, 1: compiled into the variant),
+    ``fma2`` (1: paired multiply-adds over pairs of output rows) and ``shfl``
+    (1: window values from neighbouring lanes by warp shuffles)."""
     _fields_ = [("block_x", i32), ("block_y", i32), ("tile_x", i32), ("tile_y", i32),
-                ("use_smem", i32), ("unroll", i32), ("persist", i32), ("taps", i32)]
-    PARAMS = ("block_x", "block_y", "tile_x", "tile_y", "use_smem", "unroll", "persist", "taps")
+                ("use_smem", i32), ("unroll", i32), ("persist", i32), ("taps", i32), ("fma2", i32),
+                ("shfl", i32)]
+    PARAMS = ("block_x", "block_y", "tile_x", "tile_y", "use_smem", "unroll", "persist", "taps", "fma2", "shfl")
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k in self.PARAMS}
@@ -83,7 +86,7 @@ class TuneOpts(ctypes.Structure):
                 ("warmup", i32), ("flush_l2", i32), ("compile_threads", i32), ("graph_below_us", i32),
                 ("anneal_chains", i32), ("reserved", i32), ("cache_dir", cp), ("resume_path", cp),
                 ("trace_path", cp), ("grid_modes", i32), ("remeasure_top", i32), ("remeasure_repeats", i32),
-                ("taps_imm", i32), ("remeasure_taps", i32), ("reserved3", i32)]
+                ("taps_imm", i32), ("remeasure_forms", i32), ("reserved3", i32)]
 
 
 class Row(ctypes.Structure):
@@ -118,7 +121,7 @@ class BatchOpts(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_items", i32), ("n_buckets", i32), ("n_work", i64), ("grid", i32), ("threads", i32),
                 ("smem_bytes", i32), ("regs", i32), ("plan_ms", dbl), ("tune_ms", dbl), ("compile_cpu_ms", dbl),
-                ("n_solo", i32), ("reserved", i32)]
+                ("n_solo", i32), ("n_solo_fma2", i32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -261,8 +264,9 @@ def clear_cache():
     _check(_load().ct_clear_cache())
 
 
-def config(block_x=32, block_y=8, tile_x=1, tile_y=1, use_smem=0, unroll=0, persist=0, taps=0) -> Config:
-    return Config(block_x, block_y, tile_x, tile_y, use_smem, unroll, persist, taps)
+def config(block_x=32, block_y=8, tile_x=1, tile_y=1, use_smem=0, unroll=0, persist=0, taps=0, fma2=0,
+           shfl=0) -> Config:
+    return Config(block_x, block_y, tile_x, tile_y, use_smem, unroll, persist, taps, fma2, shfl)
 
 
 def default_config() -> Config:
@@ -510,11 +514,11 @@ def _collect(t, best, write_path=None, space=None, flops=0.0) -> Table:
 
 def _opts(seed=0, sample_fraction=0.0, max_evals=0, repeats=0, warmup=0, flush_l2=False, compile_threads=0,
           graph_below_us=0, anneal_chains=0, cache_dir=None, resume_path=None, trace_path=None, grid_modes=0,
-          remeasure_top=0, remeasure_repeats=0, taps_imm=0, remeasure_taps=0):
+          remeasure_top=0, remeasure_repeats=0, taps_imm=0, remeasure_forms=0):
     return TuneOpts(seed, sample_fraction, max_evals, repeats, warmup, int(flush_l2), compile_threads,
                     graph_below_us, anneal_chains, 0, cache_dir.encode() if cache_dir else None,
                     resume_path.encode() if resume_path else None, trace_path.encode() if trace_path else None,
-                    int(grid_modes), remeasure_top, remeasure_repeats, int(taps_imm), int(remeasure_taps), 0)
+                    int(grid_modes), remeasure_top, remeasure_repeats, int(taps_imm), int(remeasure_forms), 0)
 
 
 def tune(problem: Problem, space="small", strategy="brute", *, image=None, filt=None, out=None,

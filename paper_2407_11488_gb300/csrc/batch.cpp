@@ -403,6 +403,10 @@ ct_status plan_solo(ct_batch& B, const ct_batch_opts& o, std::vector<char>& solo
         to.seed = 1;
         to.max_evals = o.solo_evals > 0 ? o.solo_evals : 60;
         to.anneal_chains = 4;
+        // the five fastest are timed again, also with paired multiply-adds (a
+        // form every problem of the size can share: taps stay in the parameter block)
+        to.remeasure_top = 5;
+        to.remeasure_forms = 2;
         ct_config best{};
         ct_table* t = nullptr;
         st = ct_tune(&p, sp, CT_ANNEAL, &to, big.d_image, big.h_filter, big.d_out, &best, &t);
@@ -653,39 +657,97 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
             return cuda_fail(e, "cudaStreamCreate");
         forks.streams.push_back(x);
     }
-    cudaGraph_t g = nullptr;
-    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-        return cuda_fail(e, "cudaStreamBeginCapture");
-    st = CT_OK;
-    if (nfs > 0) {
-        cudaEventRecord(forks.events[0], s);
-        for (size_t k = 0; k < nfs; ++k) cudaStreamWaitEvent(forks.streams[k], forks.events[0], 0);
-        for (size_t k = 0; k < B->solo_items.size() && st == CT_OK; ++k) {
-            const ct_batch_item& it = items[B->solo_items[k]];
-            const ct_problem p{it.out_w, it.out_h, it.filter_w, it.filter_h, it.in_pitch, it.out_pitch, o.dtype, 0};
-            // one block per tile: the solo launches run beside each other, and
-            // small blocks let the hardware interleave them
-            st = launch_variant(*B->solo_vars[k], p, it.d_image, it.h_filter, it.d_out, forks.streams[k % nfs], 0);
+    auto capture = [&](const std::vector<VariantPtr>& vars, cudaGraphExec_t* exec) -> ct_status {
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamBeginCapture");
+        ct_status cst = CT_OK;
+        if (nfs > 0) {
+            cudaEventRecord(forks.events[0], s);
+            for (size_t k = 0; k < nfs; ++k) cudaStreamWaitEvent(forks.streams[k], forks.events[0], 0);
+            for (size_t k = 0; k < B->solo_items.size() && cst == CT_OK; ++k) {
+                const ct_batch_item& it = items[B->solo_items[k]];
+                const ct_problem p{it.out_w, it.out_h, it.filter_w, it.filter_h, it.in_pitch, it.out_pitch, o.dtype, 0};
+                // one block per tile: the solo launches run beside each other, and
+                // small blocks let the hardware interleave them
+                cst = launch_variant(*vars[k], p, it.d_image, it.h_filter, it.d_out, forks.streams[k % nfs], 0);
+            }
+            for (size_t k = 0; k < nfs; ++k) {
+                cudaEventRecord(forks.events[k + 1], forks.streams[k]);
+                cudaStreamWaitEvent(s, forks.events[k + 1], 0);
+            }
         }
-        for (size_t k = 0; k < nfs; ++k) {
-            cudaEventRecord(forks.events[k + 1], forks.streams[k]);
-            cudaStreamWaitEvent(s, forks.events[k + 1], 0);
+        if (cst == CT_OK && persistent) {
+            DevParams prm{B->d_probs, B->d_work, B->d_filters, B->d_tmaps, B->d_counter, (int32_t)B->n_work, 0};
+            cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned), s);
+            cst = launch_batch(*B->module, B->grid, threads, prm, s);
+        }
+        ce = cudaStreamEndCapture(s, &g);
+        if (cst != CT_OK || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return cst != CT_OK ? cst : cuda_fail(ce, "cudaStreamEndCapture");
+        }
+        ce = cudaGraphInstantiate(exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+        return CT_OK;
+    };
+    if ((st = capture(B->solo_vars, &B->exec)) != CT_OK) return st;
+    // Solo launches in the paired multiply-add form are faster alone but may
+    // overlap worse with their neighbours: when the plan has any, the graph is
+    // also captured with their scalar twins, both graphs are timed (replays,
+    // interleaved, median of 5 after 2 warm-ups; this writes every output) and
+    // the faster is kept.
+    std::vector<VariantPtr> scalar = B->solo_vars;
+    bool any_pair = false;
+    for (size_t k = 0; k < scalar.size(); ++k) {
+        if (!scalar[k]->key.cfg.fma2) continue;
+        any_pair = true;
+        VariantKey sk = scalar[k]->key;
+        sk.cfg.fma2 = 0;
+        VariantPtr v = get_variant(sk);
+        if (!v || v->status != CT_OK || (st = load_variant(*v)) != CT_OK)
+            return fail(CT_ERR_COMPILE, "scalar twin of a solo variant: %s", v ? v->error.c_str() : "none");
+        scalar[k] = v;
+    }
+    if (any_pair) {
+        cudaGraphExec_t alt = nullptr;
+        if ((st = capture(scalar, &alt)) != CT_OK) return st;
+        cudaEvent_t ev[4];
+        for (auto& x : ev) cudaEventCreate(&x);
+        std::vector<float> ta, tb;
+        for (int r = 0; r < 7; ++r) {
+            cudaEventRecord(ev[0], s);
+            cudaGraphLaunch(B->exec, s);
+            cudaEventRecord(ev[1], s);
+            cudaGraphLaunch(alt, s);
+            cudaEventRecord(ev[2], s);
+            if ((e = cudaEventSynchronize(ev[2])) != cudaSuccess) {
+                for (auto& x : ev) cudaEventDestroy(x);
+                cudaGraphExecDestroy(alt);
+                return cuda_fail(e, "timing the batch graph forms");
+            }
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, ev[0], ev[1]);
+            cudaEventElapsedTime(&b, ev[1], ev[2]);
+            if (r >= 2) {
+                ta.push_back(a);
+                tb.push_back(b);
+            }
+        }
+        for (auto& x : ev) cudaEventDestroy(x);
+        std::sort(ta.begin(), ta.end());
+        std::sort(tb.begin(), tb.end());
+        if (tb[tb.size() / 2] < ta[ta.size() / 2]) {
+            cudaGraphExecDestroy(B->exec);
+            B->exec = alt;
+            B->solo_vars = scalar;
+        } else {
+            cudaGraphExecDestroy(alt);
         }
     }
-    if (st == CT_OK && persistent) {
-        DevParams prm{B->d_probs, B->d_work, B->d_filters, B->d_tmaps, B->d_counter, (int32_t)B->n_work, 0};
-        cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned), s);
-        st = launch_batch(*B->module, B->grid, threads, prm, s);
-    }
-    e = cudaStreamEndCapture(s, &g);
-    if (st != CT_OK || e != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        cudaGetLastError();
-        return st != CT_OK ? st : cuda_fail(e, "cudaStreamEndCapture");
-    }
-    e = cudaGraphInstantiate(&B->exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    for (const auto& v : B->solo_vars) B->info.n_solo_fma2 += v->key.cfg.fma2 ? 1 : 0;
     B->info.n_items = n;
     B->info.n_buckets = (int32_t)B->buckets.size();
     B->info.n_work = B->n_work;

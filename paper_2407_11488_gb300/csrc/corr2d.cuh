@@ -35,6 +35,21 @@
 //                  CT_TAP_VALUES (FH*FW float literals, row-major), so every
 //                  multiply-add takes its tap as an immediate operand; 0: the
 //                  taps come from the parameter block
+//   CT_SHFL        1 (with CT_SMEM = 1, CT_BX a multiple of 32, CT_TX a
+//                  multiple of 4): a thread reads only its own TX values of an
+//                  input row from shared memory and takes the other WW - TX
+//                  values of its window from the lanes to its right with warp
+//                  shuffles (a warp is 32 consecutive threads of one thread
+//                  row); a lane whose window runs past the warp's last lane
+//                  then reads its whole window itself.  The same values reach
+//                  the same registers, so the bits are unchanged
+//   CT_FMA2        1 (with CT_UNROLL = 1, CT_TY >= 2, CT_TAPS_IMM = 0): output
+//                  rows 2k and 2k+1 of a thread pair up; an input row feeds
+//                  both through one paired FP32 multiply-add (fma.rn.f32x2)
+//                  per column and tap, with the tap pair (f[i][j], f[i-1][j])
+//                  from the parameter block.  Each half is an ordinary fma.rn,
+//                  and every output still adds its taps in (i, j) order, so
+//                  the bits are those of the scalar form
 //
 // Layout contract (checked by the host before launch): row pitches are in
 // elements and make every row start on a 16-byte boundary; the image buffer
@@ -71,6 +86,18 @@
 #if CT_TAPS_IMM && !CT_UNROLL
 #error "compiled-in taps need the unrolled body"
 #endif
+#ifndef CT_FMA2
+#define CT_FMA2 0
+#endif
+#if CT_FMA2 && (!CT_UNROLL || CT_TY < 2 || CT_TAPS_IMM)
+#error "paired multiply-adds need the unrolled body, two output rows per thread and parameter-block taps"
+#endif
+#ifndef CT_SHFL
+#define CT_SHFL 0
+#endif
+#if CT_SHFL && (!CT_SMEM || CT_BX % 32 != 0 || CT_TX % 4 != 0)
+#error "shuffled windows need shared-memory staging, whole warps per thread row and 4-wide register tiles"
+#endif
 
 #ifdef CT_INJECT_COMPILE_ERROR
 #error "compile failure requested through CT_INJECT_COMPILE_ERROR"
@@ -78,6 +105,7 @@
 
 typedef long long ct_i64;
 typedef unsigned int ct_u32;
+typedef unsigned long long ct_u64;
 
 #if CT_DTYPE == 0
 typedef float ct_in_t;
@@ -104,6 +132,9 @@ struct CtParams {
     int step_x, step_y; // persistent: gridDim.x as (tile columns, tile rows) of the row-major order
     int pad_;
     float f[CT_FH * CT_FW];
+#if CT_FMA2
+    ct_u64 fp[CT_FH * CT_FW];   // entry i*FW+j, i >= 1: f[i][j] in the low half, f[i-1][j] in the high half
+#endif
 };
 
 #define CT_NT (CT_BX * CT_BY)
@@ -209,6 +240,26 @@ __device__ __forceinline__ bool ct_bar_wait(unsigned long long* bar, unsigned pa
 
 #endif
 
+#if CT_FMA2
+__device__ __forceinline__ ct_u64 ct_pk(float lo, float hi)
+{
+    ct_u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void ct_upk(ct_u64 r, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+// d = a * b + c in each half, each an fma.rn.f32
+__device__ __forceinline__ ct_u64 ct_fma2(ct_u64 a, ct_u64 b, ct_u64 c)
+{
+    ct_u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+#endif
+
 __device__ __forceinline__ void ct_row_shared(float (&w)[CT_WWV], const float* __restrict__ s)
 {
 #pragma unroll
@@ -224,6 +275,23 @@ __device__ __forceinline__ void ct_row_shared(float (&w)[CT_WWV], const float* _
         }
     }
 }
+
+#if CT_SHFL
+// The window of a lane from its own TX values and its right-hand neighbours'
+// (lane + d holds columns d*TX .. d*TX+TX-1 past this lane's first column).
+__device__ __forceinline__ void ct_row_shfl(float (&w)[CT_WWV], const float* __restrict__ s, unsigned lane)
+{
+#pragma unroll
+    for (int k = 0; k < CT_TX; k += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(s + k);
+        w[k] = v.x; w[k + 1] = v.y; w[k + 2] = v.z; w[k + 3] = v.w;
+    }
+#pragma unroll
+    for (int m = 0; m < CT_WW - CT_TX; ++m)
+        w[CT_TX + m] = __shfl_down_sync(0xffffffffu, w[m % CT_TX], 1 + m / CT_TX);
+    if (lane + (CT_WW - 1) / CT_TX > 31u) ct_row_shared(w, s);   // past the warp: read it all
+}
+#endif
 
 extern "C" __global__ void __launch_bounds__(CT_NT)
 ct_corr2d(const __grid_constant__ CtParams p)
@@ -244,6 +312,12 @@ ct_corr2d(const __grid_constant__ CtParams p)
 #define CT_TAP(k) p.f[k]
 #endif
 
+#if CT_SHFL
+    const unsigned lane = threadIdx.x & 31u;
+#define CT_ROW_SMEM(w, s) ct_row_shfl(w, s, lane)
+#else
+#define CT_ROW_SMEM(w, s) ct_row_shared(w, s)
+#endif
 #if CT_SMEM && CT_TMA
     extern __shared__ float4 ct_smem4[];
     __shared__ unsigned long long ct_bar;
@@ -256,11 +330,11 @@ ct_corr2d(const __grid_constant__ CtParams p)
     }
     __syncthreads();   // the barrier is initialised before anyone waits on it
     unsigned phase = 0u;
-#define CT_LOAD_ROW(w, r) ct_row_shared(w, sm + (ly + (r)) * CT_SW + lx)
+#define CT_LOAD_ROW(w, r) CT_ROW_SMEM(w, sm + (ly + (r)) * CT_SW + lx)
 #elif CT_SMEM
     extern __shared__ float4 ct_smem4[];
     float* sm = reinterpret_cast<float*>(ct_smem4);
-#define CT_LOAD_ROW(w, r) ct_row_shared(w, sm + (ly + (r)) * CT_SW + lx)
+#define CT_LOAD_ROW(w, r) CT_ROW_SMEM(w, sm + (ly + (r)) * CT_SW + lx)
 #else
 #define CT_LOAD_ROW(w, r) ct_row_global(w, p, gy + (r), gx)
 #endif
@@ -325,7 +399,67 @@ ct_corr2d(const __grid_constant__ CtParams p)
 #pragma unroll
                 for (int tx = 0; tx < CT_TX; ++tx) acc[ty][tx] = 0.0f;
 
-#if CT_UNROLL
+#if CT_UNROLL && CT_FMA2
+            // Output rows 2k and 2k+1 pair up: input row r feeds them with
+            // filter rows i = r - 2k and i - 1.  Where both exist one paired
+            // multiply-add per (pair, column, tap) does both; at the two ends
+            // of a pair's input rows only one of them exists (scalar FMA).
+            ct_u64 acc2[CT_TY / 2][CT_TX];
+#pragma unroll
+            for (int k = 0; k < CT_TY / 2; ++k)
+#pragma unroll
+                for (int tx = 0; tx < CT_TX; ++tx) acc2[k][tx] = ct_pk(0.0f, 0.0f);
+#pragma unroll
+            for (int r = 0; r < CT_TY + CT_FH - 1; ++r) {
+                float w[CT_WWV];
+                CT_LOAD_ROW(w, r);
+#pragma unroll
+                for (int k = 0; k < CT_TY / 2; ++k) {
+                    const int i = r - 2 * k;
+                    if (i >= 1 && i < CT_FH) {
+#pragma unroll
+                        for (int j = 0; j < CT_FW; ++j) {
+                            const ct_u64 fv = p.fp[i * CT_FW + j];
+#pragma unroll
+                            for (int tx = 0; tx < CT_TX; ++tx)
+                                acc2[k][tx] = ct_fma2(ct_pk(w[tx + j], w[tx + j]), fv, acc2[k][tx]);
+                        }
+                    } else if (i == 0 || i == CT_FH) {
+                        const int fi = i == 0 ? 0 : CT_FH - 1;
+#pragma unroll
+                        for (int j = 0; j < CT_FW; ++j) {
+                            const float fv = p.f[fi * CT_FW + j];
+#pragma unroll
+                            for (int tx = 0; tx < CT_TX; ++tx) {
+                                float lo, hi;
+                                ct_upk(acc2[k][tx], lo, hi);
+                                if (i == 0) lo = fmaf(w[tx + j], fv, lo);
+                                else hi = fmaf(w[tx + j], fv, hi);
+                                acc2[k][tx] = ct_pk(lo, hi);
+                            }
+                        }
+                    }
+                }
+#if CT_TY % 2
+                {   // the last output row has no partner
+                    const int i = r - (CT_TY - 1);
+                    if (i >= 0 && i < CT_FH) {
+#pragma unroll
+                        for (int j = 0; j < CT_FW; ++j) {
+                            const float fv = p.f[i * CT_FW + j];
+#pragma unroll
+                            for (int tx = 0; tx < CT_TX; ++tx)
+                                acc[CT_TY - 1][tx] = fmaf(w[tx + j], fv, acc[CT_TY - 1][tx]);
+                        }
+                    }
+                }
+#endif
+            }
+#pragma unroll
+            for (int k = 0; k < CT_TY / 2; ++k)
+#pragma unroll
+                for (int tx = 0; tx < CT_TX; ++tx) ct_upk(acc2[k][tx], acc[2 * k][tx], acc[2 * k + 1][tx]);
+#elif CT_UNROLL
             // Input row r feeds output rows ty with filter row i = r - ty.
 #pragma unroll
             for (int r = 0; r < CT_TY + CT_FH - 1; ++r) {
@@ -407,5 +541,6 @@ ct_corr2d(const __grid_constant__ CtParams p)
 #endif
     }
 #undef CT_LOAD_ROW
+#undef CT_ROW_SMEM
 #undef CT_TAP
 }

@@ -398,7 +398,7 @@ static std::string row_json(const ct_row& r, const std::string& tag)
     std::ostringstream os;
     os << "{\"problem\":\"" << tag << "\",\"index\":" << r.index;
     for (int k = 0; k < 6; ++k) os << ",\"" << kParamNames[k] << "\":" << cfg_get(r.cfg, k);
-    os << ",\"persist\":" << r.cfg.persist << ",\"taps\":" << r.cfg.taps;
+    os << ",\"persist\":" << r.cfg.persist << ",\"taps\":" << r.cfg.taps << ",\"fma2\":" << r.cfg.fma2 << ",\"shfl\":" << r.cfg.shfl;
     os << ",\"status\":" << r.status << ",\"n\":" << r.n << ",\"t_med_ms\":";
     fmt_num(os, r.t_med_ms);
     os << ",\"t_min_ms\":";
@@ -853,11 +853,13 @@ static ct_status run_strategy(const ct_problem& p, const Space& s, ct_strategy s
 // keep their graph-timed figures) with `reps` launches each, interleaved
 // round by round so that a clock change affects every candidate alike, each
 // launch bracketed by events and preceded by the L2 flush when one is given.
-// With both_taps, an unrolled row is timed in both tap forms (parameter
-// block and compiled in) and keeps the faster (cfg.taps records it).
+// forms bit 0: an unrolled row is also timed in its other tap form (parameter
+// block / compiled in); bit 1: also in the paired multiply-add form (two
+// output rows per thread or more).  Each row keeps its fastest form
+// (cfg.taps, cfg.fma2 record it).
 // best_row becomes the fastest by the re-measured median.  Returns the
 // variant of that row (null when nothing was re-measured).
-static VariantPtr remeasure(ct_table& t, const ct_problem& p, int k, int reps, double min_ms, bool both_taps,
+static VariantPtr remeasure(ct_table& t, const ct_problem& p, int k, int reps, double min_ms, int forms,
                             const void* img, const void* filt, float* out, void* flush, int64_t flush_bytes,
                             cudaStream_t s, CompilePool& pool)
 {
@@ -881,11 +883,25 @@ static VariantPtr remeasure(ct_table& t, const ct_problem& p, int k, int reps, d
     };
     std::vector<Cand> cand;
     for (size_t i : order) {
-        cand.push_back({i, t.rows[i].cfg, nullptr, {}});
-        if (both_taps && t.rows[i].cfg.unroll) {
-            ct_config alt = t.rows[i].cfg;
+        const ct_config c = t.rows[i].cfg;
+        cand.push_back({i, c, nullptr, {}});
+        if ((forms & 1) && c.unroll) {
+            ct_config alt = c;
             alt.taps = alt.taps ? 0 : 1;
-            if (variant_key(p, alt, filt).cfg.taps == alt.taps) cand.push_back({i, alt, nullptr, {}});
+            alt.fma2 = 0;
+            const VariantKey vk = variant_key(p, alt, filt);
+            if (vk.cfg.taps == alt.taps && vk.cfg.fma2 == 0) cand.push_back({i, alt, nullptr, {}});
+        }
+        if ((forms & 2) && c.unroll && !c.fma2) {
+            ct_config alt = c;
+            alt.taps = 0;
+            alt.fma2 = 1;
+            if (variant_key(p, alt, filt).cfg.fma2 == 1) cand.push_back({i, alt, nullptr, {}});
+        }
+        if ((forms & 4) && !c.shfl) {
+            ct_config alt = c;
+            alt.shfl = 1;
+            if (variant_key(p, alt, filt).cfg.shfl == 1) cand.push_back({i, alt, nullptr, {}});
         }
     }
     std::vector<std::shared_future<VariantPtr>> futs;
@@ -927,6 +943,8 @@ static VariantPtr remeasure(ct_table& t, const ct_problem& p, int k, int reps, d
         if (!std::isfinite(row.t_remeasured_ms) || m.med < row.t_remeasured_ms) {
             row.t_remeasured_ms = m.med;
             row.cfg.taps = c.cfg.taps;
+            row.cfg.fma2 = c.cfg.fma2;
+            row.cfg.shfl = c.cfg.shfl;
             var_of[c.row] = c.v;
         }
     }
@@ -1077,7 +1095,7 @@ ct_status tune_gpu(const ct_problem* p, const ct_space* s, ct_strategy st, const
         VariantPtr re;
         if (rc == CT_OK && o.remeasure_top > 0)
             re = remeasure(*t, *p, o.remeasure_top, o.remeasure_repeats, std::max(0.0, to.graph_below_ms),
-                           o.remeasure_taps != 0, img, h_filter, out, o.flush_l2 ? flush : nullptr, flush_bytes,
+                           o.remeasure_forms, img, h_filter, out, o.flush_l2 ? flush : nullptr, flush_bytes,
                            stream, pool);
         if (rc == CT_OK && re) put_variant(re);
         else if (rc == CT_OK && ev.best()) put_variant(ev.best());

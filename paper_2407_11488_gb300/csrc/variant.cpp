@@ -38,6 +38,8 @@ uint64_t VariantKey::packed() const
     k = k * 64 + (uint64_t)fw;
     k = k * 64 + (uint64_t)fh;
     k = k * 4 + (uint64_t)dtype;
+    k = k * 2 + (uint64_t)(cfg.fma2 ? 1 : 0);
+    k = k * 2 + (uint64_t)(cfg.shfl ? 1 : 0);
     if (!taps.empty()) {   // a filter-specific variant: mix in the taps' bits
         uint64_t h = 1469598103934665603ull;
         const unsigned char* b = reinterpret_cast<const unsigned char*>(taps.data());
@@ -54,7 +56,11 @@ VariantKey variant_key(const ct_problem& p, const ct_config& c, const void* h_fi
 {
     VariantKey k{c, p.filter_w, p.filter_h, p.dtype, {}};
     k.cfg.persist = 0;
-    if (!(c.taps && c.unroll && h_filter)) {
+    // paired multiply-adds: unrolled, two output rows per thread, parameter-block taps
+    k.cfg.fma2 = (c.fma2 && c.unroll && c.tile_y >= 2 && !c.taps) ? 1 : 0;
+    // shuffled windows: staged halo, whole warps per thread row, 4-wide register tiles
+    k.cfg.shfl = (c.shfl && c.use_smem && c.block_x % 32 == 0 && c.tile_x % 4 == 0) ? 1 : 0;
+    if (!(c.taps && c.unroll && h_filter) || k.cfg.fma2) {
         k.cfg.taps = 0;
         return k;
     }
@@ -82,9 +88,9 @@ VariantKey variant_key(const ct_problem& p, const ct_config& c, const void* h_fi
 std::string VariantKey::describe() const
 {
     char b[160];
-    snprintf(b, sizeof b, "bx=%d by=%d tx=%d ty=%d smem=%d unroll=%d fw=%d fh=%d dtype=%d%s", cfg.block_x,
+    snprintf(b, sizeof b, "bx=%d by=%d tx=%d ty=%d smem=%d unroll=%d fw=%d fh=%d dtype=%d%s%s", cfg.block_x,
              cfg.block_y, cfg.tile_x, cfg.tile_y, cfg.use_smem, cfg.unroll, fw, fh, dtype,
-             taps.empty() ? "" : " taps=compiled");
+             taps.empty() ? "" : " taps=compiled", cfg.fma2 ? " fma2" : cfg.shfl ? " shfl" : "");
     return b;
 }
 
@@ -121,6 +127,8 @@ static std::vector<std::string> nvrtc_options(const VariantKey& k)
     def("CT_DTYPE", k.dtype);
     def("CT_TMA", tma_staged(k.cfg, k.fw, k.fh, k.dtype) ? 1 : 0);
     if (!k.taps.empty()) def("CT_TAPS_IMM", 1);
+    if (k.cfg.fma2) def("CT_FMA2", 1);
+    if (k.cfg.shfl) def("CT_SHFL", 1);
     add_env_options(o);
     return o;
 }
@@ -525,9 +533,12 @@ ct_status check_buffers(const ct_problem& p, const void* d_image, const void* h_
 // not use it), in, out, in_pitch, out_pitch (8 bytes each), out_w, out_h,
 // in_w, in_h (4 bytes each), the error word's address (8 bytes), tiles_x,
 // n_tiles, persist, step_x, step_y and one spare (4 bytes each), then
-// filter_h*filter_w floats; the struct's size is a multiple of 64 bytes.
+// filter_h*filter_w floats, then (paired multiply-add variants) at the next
+// 8-byte boundary filter_h*filter_w tap pairs of 8 bytes; the struct's size
+// is a multiple of 64 bytes.
 static constexpr size_t kParamHeader = 208;
-static constexpr size_t kParamMax = (kParamHeader + 4 * CT_MAX_FILTER * CT_MAX_FILTER + 63) / 64 * 64;
+static constexpr size_t kParamMax =
+    (kParamHeader + 4 * CT_MAX_FILTER * CT_MAX_FILTER + 8 + 8 * CT_MAX_FILTER * CT_MAX_FILTER + 63) / 64 * 64;
 
 int64_t tile_count(const ct_problem& p, const ct_config& c)
 {
@@ -582,6 +593,15 @@ ct_status launch_variant(Variant& v, const ct_problem& p, const void* d_image, c
             uint32_t u = (uint32_t)hb[i] << 16;
             memcpy(&taps[i], &u, 4);
         }
+    }
+    if (v.key.cfg.fma2) {   // tap pairs (f[i][j], f[i-1][j]) for i >= 1
+        unsigned char* fp = buf + round_up((int64_t)(kParamHeader + 4 * (size_t)nt), 8);
+        memset(fp, 0, 8 * (size_t)p.filter_w);   // row 0 has no pair
+        for (int i = 1; i < p.filter_h; ++i)
+            for (int j = 0; j < p.filter_w; ++j) {
+                memcpy(fp + 8 * (size_t)(i * p.filter_w + j), &taps[i * p.filter_w + j], 4);
+                memcpy(fp + 8 * (size_t)(i * p.filter_w + j) + 4, &taps[(i - 1) * p.filter_w + j], 4);
+            }
     }
     void* args[1] = {buf};
     const dim3 grid = persist ? dim3((unsigned)g1, 1, 1) : dim3((unsigned)gx, (unsigned)gy, 1);

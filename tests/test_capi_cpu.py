@@ -82,7 +82,7 @@ def test_space_enumeration_matches_oracle(ctlib, name, fw, fh):
         assert i1 == i2
         d = c1.as_dict()
         d["smem"] = d.pop("use_smem")
-        assert d.pop("persist") == 0 and d.pop("taps") == 0   # variant forms, not points of the space
+        assert d.pop("persist") == 0 and d.pop("taps") == 0 and d.pop("fma2") == 0 and d.pop("shfl") == 0
         assert d == c2
     raw, valid = sp.count(p, 232448)
     assert raw == len(ospace.enumerate_space(name, fw, fh, valid_only=False)) and valid == len(ref)

@@ -44,7 +44,7 @@ def _image_with_nan_rows(img, device, bf16):
     return t.to(device)[:img.shape[0]]
 
 
-def _sweep(ct, device, ow, oh, fw, fh, seed, every, bf16=False, taps=0):
+def _sweep(ct, device, ow, oh, fw, fh, seed, every, bf16=False, taps=0, fma2=0, shfl=0):
     img, f = synthetic.make_problem(seed, ow, oh, fw, fh, pad_value=np.nan, extra_pitch=8 if bf16 else 4,
                                     pitch_align=8 if bf16 else 4)
     if bf16:
@@ -62,10 +62,16 @@ def _sweep(ct, device, ow, oh, fw, fh, seed, every, bf16=False, taps=0):
     ents = ospace.enumerate_space("full", fw, fh)
     if taps:                                      # compiled-in taps apply to the unrolled variants
         ents = [e for e in ents if e[1]["unroll"]]
+    if fma2:                                      # paired multiply-adds: unrolled, two output rows or more
+        ents = [e for e in ents if e[1]["unroll"] and e[1]["tile_y"] >= 2]
+    if shfl:                                      # shuffled windows: staged halo, whole warps, 4-wide tiles
+        ents = [e for e in ents if e[1]["smem"] and e[1]["block_x"] % 32 == 0 and e[1]["tile_x"] % 4 == 0]
     ents = ents[::every]
     cfgs = [_cfg(ct, c) for _, c in ents]
     for c in cfgs:
         c.taps = taps
+        c.fma2 = fma2
+        c.shfl = shfl
     lib_cfgs = {c.space_tuple() for _, c in ct.Space("full").enumerate(p)}
     assert {c.space_tuple() for c in cfgs} <= lib_cfgs
 
@@ -151,3 +157,33 @@ def test_compiled_taps_follow_the_filter(ctlib, cuda_device):
     a, ok_a = run_config(ctlib, d_img, f3, c_imm, ow, oh, in_w=ow + fs - 1)
     b, ok_b = run_config(ctlib, d_img, f3, c_par, ow, oh, in_w=ow + fs - 1)
     assert ok_a and ok_b and np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+@pytest.mark.parametrize("case", ["f32_17x17", "f32_5x7", "bf16_9x9"])
+def test_paired_fma_same_bits(ctlib, cuda_device, case):
+    """Paired multiply-adds (ct_config.fma2 = 1, output rows 2k and 2k+1 share
+    each input row through one f32x2 FMA per column and tap): a spread of the
+    unrolled points with two or more output rows per thread (every 16th for
+    17x17, every 4th for 5x7, every 24th for BF16 9x9) matches the oracle, and
+    its bits equal those of the scalar form."""
+    ow, oh, fw, fh, bf16, every = {"f32_17x17": (333, 157, 17, 17, False, 16), "f32_5x7": (301, 163, 5, 7, False, 4),
+                                   "bf16_9x9": (259, 131, 9, 9, True, 24)}[case]
+    n2, paired = _sweep(ctlib, cuda_device, ow, oh, fw, fh, seed=25, every=every, bf16=bf16, fma2=1)
+    n0, scalar = _sweep(ctlib, cuda_device, ow, oh, fw, fh, seed=25, every=10 ** 6, bf16=bf16)
+    assert n2 >= 40 and n0 == 1
+    assert np.array_equal(paired.view(np.uint32), scalar.view(np.uint32))
+
+
+@pytest.mark.parametrize("case", ["f32_17x17", "f32_5x7", "bf16_9x9"])
+def test_shuffled_window_same_bits(ctlib, cuda_device, case):
+    """Windows assembled by warp shuffles (ct_config.shfl = 1): a spread of the
+    staged points with whole warps per thread row and 4-wide register tiles
+    (every 4th for 17x17 and 5x7, every 6th for BF16 9x9; unrolled and rolled,
+    tensor-copy and per-thread staging) matches the oracle, bit for bit the
+    same as the shared-memory windows."""
+    ow, oh, fw, fh, bf16, every = {"f32_17x17": (333, 157, 17, 17, False, 4), "f32_5x7": (301, 163, 5, 7, False, 4),
+                                   "bf16_9x9": (259, 131, 9, 9, True, 6)}[case]
+    n1, shuffled = _sweep(ctlib, cuda_device, ow, oh, fw, fh, seed=26, every=every, bf16=bf16, shfl=1)
+    n0, plain = _sweep(ctlib, cuda_device, ow, oh, fw, fh, seed=26, every=10 ** 6, bf16=bf16)
+    assert n1 >= 30 and n0 == 1
+    assert np.array_equal(shuffled.view(np.uint32), plain.view(np.uint32))

@@ -96,7 +96,7 @@ def test_tuner_times_both_grids_and_remeasures(ctlib, cuda_device):
     them by the re-measured median."""
     p = ctlib.make_problem(4096, 4096, 17, 17)     # every kernel long enough for single-launch timing
     tab = ctlib.tune(p, "full", "random", seed=5, max_evals=24, repeats=5, grid_modes=1, remeasure_top=4,
-                     remeasure_repeats=9, flush_l2=True, remeasure_taps=1)
+                     remeasure_repeats=9, flush_l2=True, remeasure_forms=3)
     ok = [r for r in tab.rows if r["status"] == 0]
     assert ok
     both = [r for r in ok if math.isfinite(r["t_persist_ms"])]
@@ -117,8 +117,17 @@ def test_tuner_times_both_grids_and_remeasures(ctlib, cuda_device):
     best = tab.rows[tab.info["best_row"]]
     assert best["t_remeasured_ms"] == min(r["t_remeasured_ms"] for r in re)
     assert tab.best.as_tuple() == best["cfg"].as_tuple()
-    for r in tab.rows:                       # the re-measurement may move an unrolled row to compiled taps
+    for r in tab.rows:                       # the re-measurement may move an unrolled row to another form
         assert r["taps"] == 0 or (r["unroll"] == 1 and math.isfinite(r["t_remeasured_ms"]))
+        assert r["fma2"] == 0 or (r["unroll"] == 1 and r["tile_y"] >= 2 and r["taps"] == 0
+                                  and math.isfinite(r["t_remeasured_ms"]))
+    # the returned configuration, in whatever form won, reproduces the oracle
+    img, f = synthetic.make_problem(1, 4096, 4096, 17, 17)
+    xs, ys = synthetic.sample_points(1, 4096, 4096, 2000)
+    ref, S = oracle.corr2d_points(img, f, xs, ys)
+    d_img = upload_image(img, cuda_device)
+    out, good = run_config(ctlib, d_img, f, tab.best, 4096, 4096)
+    assert good and np.all(np.abs(out[ys, xs] - ref) <= 1e-5 * S)
 
 
 def test_tuner_with_compiled_taps(ctlib, cuda_device):
