@@ -87,8 +87,8 @@ def parse():
                     help="give every strategy its own empty cubin cache (cold compile timings)")
     ap.add_argument("--grid-modes", type=int, default=1,
                     help="1: the tuner also times each configuration on the persistent grid")
-    ap.add_argument("--remeasure-top", type=int, default=10,
-                    help="the tuner re-measures this many of its fastest configurations")
+    ap.add_argument("--remeasure-top", type=int, default=32,
+                    help="the tuner re-measures this many of its fastest configurations, in every variant form")
     ap.add_argument("--taps-imm", type=int, default=0,
                     help="1: the sweep measures unrolled configurations with the filter compiled in (the "
                          "re-measurement tries both tap forms either way)")
@@ -404,7 +404,8 @@ def run_ours(args):
         for k, strat in enumerate(strategies):
             cdir = tempfile.mkdtemp(prefix=f"convtune-{strat}-") if args.cold_cache else None
             # L2 flushed before every timed launch (as in the timed loop below), both grid forms
-            # timed, and the 10 fastest re-measured side by side before the optimum is named
+            # timed, and the fastest (--remeasure-top) re-measured side by side in every variant
+            # form before the optimum is named
             t = ct.tune(p, space, strat, image=d_img, filt=f, out=d_out, seed=args.seed, cache_dir=cdir,
                         write_path=args.table_out if k == 0 else None, anneal_chains=args.anneal_chains,
                         flush_l2=True, grid_modes=args.grid_modes, remeasure_top=args.remeasure_top,

@@ -82,8 +82,12 @@ typedef struct {
 /* One point of the search space (Table 1 names: block_size_x, block_size_y,
  * tile_size_x, tile_size_y, use_shmem; unroll is Sec. 3's loop unrolling).
  * block_x * block_y <= 1024; 1 <= tile_x, tile_y <= 16; use_smem in {0, 1};
- * unroll in {0, 1}.  With use_smem = 1, block_x * tile_x must be a multiple
- * of 4 (the staged tile starts on a 16-byte boundary).
+ * unroll in {0, 1, 2, 4}: 0 keeps the loop over filter rows rolled, 1 unrolls
+ * the whole body (input rows slide through a register window), 2 and 4 unroll
+ * the filter-row loop by that factor (Sec. 3's partial unrolling; JSON spaces
+ * may list them, the built-in spaces use {0, 1}).  With use_smem = 1,
+ * block_x * tile_x must be a multiple of 4 (the staged tile starts on a
+ * 16-byte boundary).
  *
  * persist and taps are not points of the search space but forms of a
  * variant.  persist is chosen at launch (the same compiled variant serves both

@@ -82,10 +82,12 @@ ct_status check_config(const ct_problem& p, const ct_config& c, int smem_limit)
         return fail(CT_ERR_INVALID_CONFIG, "block %dx%d exceeds %d threads", c.block_x, c.block_y, kMaxThreads);
     if (c.tile_x < 1 || c.tile_y < 1 || c.tile_x > kMaxTile || c.tile_y > kMaxTile)
         return fail(CT_ERR_INVALID_CONFIG, "tile %dx%d outside 1..%d", c.tile_x, c.tile_y, kMaxTile);
-    if ((c.use_smem != 0 && c.use_smem != 1) || (c.unroll != 0 && c.unroll != 1) ||
+    if (c.unroll != 0 && c.unroll != 1 && c.unroll != 2 && c.unroll != 4)
+        return fail(CT_ERR_INVALID_CONFIG, "unroll must be 0 (rolled), 1 (full), 2 or 4 (partial factor)");
+    if ((c.use_smem != 0 && c.use_smem != 1) ||
         (c.persist != 0 && c.persist != 1) || (c.taps != 0 && c.taps != 1) || (c.fma2 != 0 && c.fma2 != 1) ||
         (c.shfl != 0 && c.shfl != 1))
-        return fail(CT_ERR_INVALID_CONFIG, "use_smem/unroll/persist/taps/fma2/shfl must be 0 or 1");
+        return fail(CT_ERR_INVALID_CONFIG, "use_smem/persist/taps/fma2/shfl must be 0 or 1");
     if (c.use_smem && (c.block_x * c.tile_x) % 4 != 0)
         return fail(CT_ERR_INVALID_CONFIG, "use_smem needs block_x*tile_x to be a multiple of 4");
     if (smem_limit <= 0) smem_limit = device_smem_limit();

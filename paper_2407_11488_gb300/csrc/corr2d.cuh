@@ -28,7 +28,8 @@
 //                  copies 16-byte chunks (BF16 widened to FP32 on the way)
 //   CT_UNROLL      1: fully unrolled; input rows slide through a register
 //                     window and each row feeds every output row that uses it;
-//                  0: the loop over filter rows stays rolled
+//                  0: the loop over filter rows stays rolled; 2, 4: that loop
+//                     is unrolled by this factor (partial unrolling)
 //   CT_FW, CT_FH   filter width and height
 //   CT_DTYPE       0: FP32 image; 1: BF16 image (widened to FP32 on load)
 //   CT_TAPS_IMM    1 (with CT_UNROLL = 1): the taps are compiled in, from
@@ -83,13 +84,13 @@
 #ifndef CT_TAPS_IMM
 #define CT_TAPS_IMM 0
 #endif
-#if CT_TAPS_IMM && !CT_UNROLL
+#if CT_TAPS_IMM && CT_UNROLL != 1
 #error "compiled-in taps need the unrolled body"
 #endif
 #ifndef CT_FMA2
 #define CT_FMA2 0
 #endif
-#if CT_FMA2 && (!CT_UNROLL || CT_TY < 2 || CT_TAPS_IMM)
+#if CT_FMA2 && (CT_UNROLL != 1 || CT_TY < 2 || CT_TAPS_IMM)
 #error "paired multiply-adds need the unrolled body, two output rows per thread and parameter-block taps"
 #endif
 #ifndef CT_SHFL
@@ -399,7 +400,7 @@ ct_corr2d(const __grid_constant__ CtParams p)
 #pragma unroll
                 for (int tx = 0; tx < CT_TX; ++tx) acc[ty][tx] = 0.0f;
 
-#if CT_UNROLL && CT_FMA2
+#if CT_UNROLL == 1 && CT_FMA2
             // Output rows 2k and 2k+1 pair up: input row r feeds them with
             // filter rows i = r - 2k and i - 1.  Where both exist one paired
             // multiply-add per (pair, column, tap) does both; at the two ends
@@ -459,7 +460,7 @@ ct_corr2d(const __grid_constant__ CtParams p)
             for (int k = 0; k < CT_TY / 2; ++k)
 #pragma unroll
                 for (int tx = 0; tx < CT_TX; ++tx) ct_upk(acc2[k][tx], acc[2 * k][tx], acc[2 * k + 1][tx]);
-#elif CT_UNROLL
+#elif CT_UNROLL == 1
             // Input row r feeds output rows ty with filter row i = r - ty.
 #pragma unroll
             for (int r = 0; r < CT_TY + CT_FH - 1; ++r) {
@@ -480,7 +481,11 @@ ct_corr2d(const __grid_constant__ CtParams p)
                 }
             }
 #else
+#if CT_UNROLL == 0
 #pragma unroll 1
+#else
+#pragma unroll CT_UNROLL
+#endif
             for (int i = 0; i < CT_FH; ++i) {
 #pragma unroll
                 for (int ty = 0; ty < CT_TY; ++ty) {

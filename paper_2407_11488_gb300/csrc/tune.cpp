@@ -885,14 +885,14 @@ static VariantPtr remeasure(ct_table& t, const ct_problem& p, int k, int reps, d
     for (size_t i : order) {
         const ct_config c = t.rows[i].cfg;
         cand.push_back({i, c, nullptr, {}});
-        if ((forms & 1) && c.unroll) {
+        if ((forms & 1) && c.unroll == 1) {
             ct_config alt = c;
             alt.taps = alt.taps ? 0 : 1;
             alt.fma2 = 0;
             const VariantKey vk = variant_key(p, alt, filt);
             if (vk.cfg.taps == alt.taps && vk.cfg.fma2 == 0) cand.push_back({i, alt, nullptr, {}});
         }
-        if ((forms & 2) && c.unroll && !c.fma2) {
+        if ((forms & 2) && c.unroll == 1 && !c.fma2) {
             ct_config alt = c;
             alt.taps = 0;
             alt.fma2 = 1;

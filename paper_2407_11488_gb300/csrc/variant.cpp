@@ -34,7 +34,7 @@ uint64_t VariantKey::packed() const
     k = k * 32 + (uint64_t)cfg.tile_x;
     k = k * 32 + (uint64_t)cfg.tile_y;
     k = k * 2 + (uint64_t)cfg.use_smem;
-    k = k * 2 + (uint64_t)cfg.unroll;
+    k = k * 8 + (uint64_t)cfg.unroll;
     k = k * 64 + (uint64_t)fw;
     k = k * 64 + (uint64_t)fh;
     k = k * 4 + (uint64_t)dtype;
@@ -57,10 +57,10 @@ VariantKey variant_key(const ct_problem& p, const ct_config& c, const void* h_fi
     VariantKey k{c, p.filter_w, p.filter_h, p.dtype, {}};
     k.cfg.persist = 0;
     // paired multiply-adds: unrolled, two output rows per thread, parameter-block taps
-    k.cfg.fma2 = (c.fma2 && c.unroll && c.tile_y >= 2 && !c.taps) ? 1 : 0;
+    k.cfg.fma2 = (c.fma2 && c.unroll == 1 && c.tile_y >= 2 && !c.taps) ? 1 : 0;
     // shuffled windows: staged halo, whole warps per thread row, 4-wide register tiles
     k.cfg.shfl = (c.shfl && c.use_smem && c.block_x % 32 == 0 && c.tile_x % 4 == 0) ? 1 : 0;
-    if (!(c.taps && c.unroll && h_filter) || k.cfg.fma2) {
+    if (!(c.taps && c.unroll == 1 && h_filter) || k.cfg.fma2) {
         k.cfg.taps = 0;
         return k;
     }

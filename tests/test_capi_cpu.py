@@ -95,6 +95,21 @@ def test_space_counts_named_workloads(ctlib):
     assert raw == 16 * 5 * 4 * 4 * 2 * 2
 
 
+def test_partial_unroll_factors(ctlib):
+    """unroll takes 0 (rolled), 1 (full) and the partial factors 2 and 4."""
+    p = ctlib.make_problem(128, 128, 5, 5)
+    sp = ctlib.Space('{"block_x": [32], "block_y": [8], "unroll": [0, 1, 2, 4]}')
+    assert [c.unroll for _, c in sp.enumerate(p, 232448)] == [0, 1, 2, 4]
+    for u in (0, 1, 2, 4):
+        ctlib.check_config(p, ctlib.config(32, 8, 1, 1, 0, u))
+    for u in (3, 8, -1):
+        with pytest.raises(ctlib.CTError) as e:
+            ctlib.check_config(p, ctlib.config(32, 8, 1, 1, 0, u))
+        assert e.value.status == -2
+    info = ctlib.compile_variant(p, ctlib.config(32, 8, 2, 2, 1, 4))
+    assert info["regs"] > 0
+
+
 def test_space_from_json(ctlib):
     sp = ctlib.Space('{"block_x": [32, 64], "tile_y": [1, 2, 4], "unroll": [0, 1]}')
     p = ctlib.make_problem(128, 128, 3, 3)

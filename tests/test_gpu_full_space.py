@@ -187,3 +187,31 @@ def test_shuffled_window_same_bits(ctlib, cuda_device, case):
     n0, plain = _sweep(ctlib, cuda_device, ow, oh, fw, fh, seed=26, every=10 ** 6, bf16=bf16)
     assert n1 >= 30 and n0 == 1
     assert np.array_equal(shuffled.view(np.uint32), plain.view(np.uint32))
+
+
+@pytest.mark.parametrize("fw,fh", [(17, 17), (5, 7)])
+def test_partial_unroll_same_bits(ctlib, cuda_device, fw, fh):
+    """Partial unroll factors 2 and 4 of the filter-row loop (Sec. 3) over a
+    spread of block shapes, tiles and both staging forms: every variant matches
+    the oracle and gives the bits of the rolled and fully unrolled forms."""
+    ow, oh = 301, 163
+    img, f = synthetic.make_problem(27, ow, oh, fw, fh, pad_value=np.nan, extra_pitch=4)
+    ref, S = oracle.corr2d_f64(img, f, ow, oh)
+    d_img = _image_with_nan_rows(img, cuda_device, False)
+    p = ctlib.problem_for(d_img, f, in_w=ow + fw - 1)
+    sp = ctlib.Space('{"block_x": [16, 32], "block_y": [4, 8], "tile_x": [1, 2, 4], "tile_y": [1, 3], '
+                     '"use_smem": [0, 1], "unroll": [0, 1, 2, 4]}')
+    cfgs = [c for _, c in sp.enumerate(p)]
+    assert len(cfgs) == 2 * 2 * 3 * 2 * 2 * 4
+    with cf.ThreadPoolExecutor(os.cpu_count() or 8) as ex:
+        list(ex.map(lambda c: ctlib.compile_variant(p, c), cfgs))
+    first = None
+    for c in cfgs:
+        out, ok = run_config(ctlib, d_img, f, c, ow, oh, in_w=ow + fw - 1)
+        assert ok, f"guard band overwritten by {c}"
+        assert_parity(out, ref, S, repr(c))
+        if first is None:
+            first = out
+        else:
+            assert np.array_equal(out.view(np.uint32), first.view(np.uint32)), f"{c} differs bitwise"
+    ctlib.clear_cache()
