@@ -89,6 +89,8 @@ def parse():
                     help="1: the tuner also times each configuration on the persistent grid")
     ap.add_argument("--remeasure-top", type=int, default=32,
                     help="the tuner re-measures this many of its fastest configurations, in every variant form")
+    ap.add_argument("--sweep-fma2", type=int, default=0,
+                    help="1: the sweep measures every configuration that admits it with paired multiply-adds")
     ap.add_argument("--taps-imm", type=int, default=0,
                     help="1: the sweep measures unrolled configurations with the filter compiled in (the "
                          "re-measurement tries both tap forms either way)")
@@ -409,7 +411,7 @@ def run_ours(args):
             t = ct.tune(p, space, strat, image=d_img, filt=f, out=d_out, seed=args.seed, cache_dir=cdir,
                         write_path=args.table_out if k == 0 else None, anneal_chains=args.anneal_chains,
                         flush_l2=True, grid_modes=args.grid_modes, remeasure_top=args.remeasure_top,
-                        taps_imm=args.taps_imm, remeasure_forms=7)
+                        taps_imm=args.taps_imm, remeasure_forms=7, sweep_fma2=args.sweep_fma2)
             brow = t.rows[t.info["best_row"]]
             tuning[strat] = dict(t.info, best=t.best.as_dict(), best_ms=brow["t_med_ms"],
                                  best_remeasured_ms=brow["t_remeasured_ms"], best_sm_mhz=brow["sm_mhz"])
@@ -622,7 +624,9 @@ def run_ours(args):
             "bit_identical_to_plain": bm["identical"], "composite_bound_ms": bm["peak_s"] * 1e3,
             "frac_of_bound": bm["peak_s"] * 1e3 / bm["t_b"], "n_solo": bm["binfo"]["n_solo"],
             "n_buckets": bm["binfo"]["n_buckets"], "plan_s": bm["plan_s"], "plain_tune_s": bm["plain_tune_s"],
-            "e2e_gflops": bm["flops"] / bm["te"] / 1e9, "clocks": bm["clocks"]}
+            "e2e_gflops": bm["flops"] / bm["te"] / 1e9, "clocks": bm["clocks"],
+            "n_solo_fma2": bm["binfo"].get("n_solo_fma2"),
+            "plain_form_choice": bm["tuning"].get("plain_form_choice")}
         line["batched_p50_ms"] = bm["p50"]
         line["batched_p99_ms"] = bm["p99"]
         line["batched_vs_plain"] = bm["t_p"] / bm["t_b"]
@@ -723,11 +727,43 @@ def measure_batch(args, ct, dev, info, pk, fp32_peak, world, plain_cfg=None):
         tuning[f"plain_f{fs}"] = {"side": side, "best": tab.best.as_dict(), "wall_s": tab.info["wall_ms"] / 1e3,
                                   "evals": tab.info["n_rows"]}
     plain_tune_s = time.time() - t0
-    plain_args = []
-    for img, f, d_img, out, side, fs in (probs if args.batch_plain == "tune" else []):
-        pr = ct.problem_for(d_img, f, in_w=side + fs - 1)
-        pr.out_pitch = out.stride(0)
-        plain_args.append((pr, cfg_for[fs], d_img.data_ptr(), f, out.data_ptr()))
+
+    def plain_launches(cfgs):
+        res = []
+        for img, f, d_img, out, side, fs in (probs if args.batch_plain == "tune" else []):
+            pr = ct.problem_for(d_img, f, in_w=side + fs - 1)
+            pr.out_pitch = out.stride(0)
+            res.append((pr, cfgs[fs], d_img.data_ptr(), f, out.data_ptr()))
+        return res
+    plain_args = plain_launches(cfg_for)
+    # a size's configuration tuned on its largest problem may have won in the paired
+    # multiply-add form; the per-problem path then also runs with the scalar twins, eagerly,
+    # and keeps whichever set is faster over the whole workload (the batch plan makes the
+    # same choice for its graph)
+    plain_form = "as tuned"
+    if any(c.fma2 for c in cfg_for.values()):
+        scalar_for = {k: ct.config(*c.as_tuple()[:8], fma2=0, shfl=c.shfl) for k, c in cfg_for.items()}
+        alt_args = plain_launches(scalar_for)
+        s_try = torch.cuda.Stream(device=dev)
+
+        def eager(args_):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(s_try):
+                for pr, cfg, di, f, do in args_:          # warm (and compile)
+                    ct.conv2d_raw(pr, cfg, di, f, do, s_try.cuda_stream)
+                ts = []
+                for _ in range(5):
+                    ev0.record(s_try)
+                    for pr, cfg, di, f, do in args_:
+                        ct.conv2d_raw(pr, cfg, di, f, do, s_try.cuda_stream)
+                    ev1.record(s_try)
+                    ev1.synchronize()
+                    ts.append(ev0.elapsed_time(ev1))
+            return statistics.median(ts)
+        t_tuned, t_scalar = eager(plain_args), eager(alt_args)
+        if t_scalar < t_tuned:
+            plain_args, cfg_for, plain_form = alt_args, scalar_for, "scalar twins of the tuned configurations"
+        tuning["plain_form_choice"] = {"as_tuned_ms": t_tuned, "scalar_ms": t_scalar, "kept": plain_form}
 
     t0 = time.time()
     batch = ct.Batch([(d_img, f, out, side + fs - 1) for (_, f, d_img, out, side, fs) in probs], tune=True,

@@ -337,7 +337,9 @@ typedef struct {
                                  paired multiply-add form (fma2); bit 2: also with
                                  shuffled windows (shfl); each row keeps its fastest
                                  form (cfg.taps, cfg.fma2, cfg.shfl) */
-    int32_t reserved3;
+    int32_t sweep_fma2;       /* 1: the strategy measures every configuration that
+                                 admits it in the paired multiply-add form (cfg.fma2 = 1
+                                 in its row) instead of the scalar one */
 } ct_tune_opts;
 
 /* One row of a timing table. */

@@ -86,7 +86,7 @@ class TuneOpts(ctypes.Structure):
                 ("warmup", i32), ("flush_l2", i32), ("compile_threads", i32), ("graph_below_us", i32),
                 ("anneal_chains", i32), ("reserved", i32), ("cache_dir", cp), ("resume_path", cp),
                 ("trace_path", cp), ("grid_modes", i32), ("remeasure_top", i32), ("remeasure_repeats", i32),
-                ("taps_imm", i32), ("remeasure_forms", i32), ("reserved3", i32)]
+                ("taps_imm", i32), ("remeasure_forms", i32), ("sweep_fma2", i32)]
 
 
 class Row(ctypes.Structure):
@@ -514,11 +514,12 @@ def _collect(t, best, write_path=None, space=None, flops=0.0) -> Table:
 
 def _opts(seed=0, sample_fraction=0.0, max_evals=0, repeats=0, warmup=0, flush_l2=False, compile_threads=0,
           graph_below_us=0, anneal_chains=0, cache_dir=None, resume_path=None, trace_path=None, grid_modes=0,
-          remeasure_top=0, remeasure_repeats=0, taps_imm=0, remeasure_forms=0):
+          remeasure_top=0, remeasure_repeats=0, taps_imm=0, remeasure_forms=0, sweep_fma2=0):
     return TuneOpts(seed, sample_fraction, max_evals, repeats, warmup, int(flush_l2), compile_threads,
                     graph_below_us, anneal_chains, 0, cache_dir.encode() if cache_dir else None,
                     resume_path.encode() if resume_path else None, trace_path.encode() if trace_path else None,
-                    int(grid_modes), remeasure_top, remeasure_repeats, int(taps_imm), int(remeasure_forms), 0)
+                    int(grid_modes), remeasure_top, remeasure_repeats, int(taps_imm), int(remeasure_forms),
+                    int(sweep_fma2))
 
 
 def tune(problem: Problem, space="small", strategy="brute", *, image=None, filt=None, out=None,

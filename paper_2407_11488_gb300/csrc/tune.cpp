@@ -122,6 +122,7 @@ struct Measure {
     double t_tiles = NAN, t_persist = NAN;  // medians per grid
     int persist = 0;                        // the faster grid
     int taps = 0;                           // 1: measured with the taps compiled in
+    int fma2 = 0;                           // 1: measured with paired multiply-adds
     int sm_mhz = 0;
     int regs = 0, spill = 0;
     int64_t smem = 0;
@@ -182,6 +183,7 @@ struct TimeOpts {
     double graph_below_ms = 0.05;
     int grid_modes = 0;   // 1: also time the persistent grid
     int taps_imm = 0;     // 1: unrolled variants get the problem's taps compiled in
+    int sweep_fma2 = 0;   // 1: variants that admit it are measured with paired multiply-adds
 };
 
 class GpuEvaluator : public Evaluator {
@@ -201,6 +203,7 @@ public:
     {
         ct_config c = e.cfg;
         c.taps = o_.taps_imm ? 1 : 0;
+        c.fma2 = o_.sweep_fma2 ? 1 : 0;
         return variant_key(p_, c, filt_);
     }
     void prefetch(const Entry& e, bool urgent) override { pool_.request(key(e), urgent); }
@@ -224,6 +227,7 @@ public:
         m.smem = v->smem;
         m.compile_ms = v->compile_ms;
         m.taps = k.taps.empty() ? 0 : 1;
+        m.fma2 = k.cfg.fma2;
         compile_cpu_ms += v->compile_ms;
         if (v->status != CT_OK) {
             m.status = v->status;
@@ -466,6 +470,9 @@ static std::unordered_map<uint64_t, Measure> read_resume(const char* path, const
         json_num(line, "persist", pe);
         json_num(line, "taps", tk);
         m.taps = tk == 1.0 ? 1 : 0;
+        double f2 = 0;
+        json_num(line, "fma2", f2);
+        m.fma2 = f2 == 1.0 ? 1 : 0;
         if (!json_num(line, "t_tiles_ms", tt)) tt = m.med;
         json_num(line, "t_persist_ms", tp);
         json_num(line, "sm_mhz", mhz);
@@ -543,6 +550,7 @@ public:
         r.cfg = e.cfg;
         r.cfg.persist = m.status == CT_OK ? m.persist : 0;
         r.cfg.taps = m.taps;
+        r.cfg.fma2 = m.fma2;
         r.t_tiles_ms = m.status == CT_OK ? m.t_tiles : NAN;
         r.t_persist_ms = m.status == CT_OK ? m.t_persist : NAN;
         r.t_remeasured_ms = NAN;
@@ -1081,6 +1089,7 @@ ct_status tune_gpu(const ct_problem* p, const ct_space* s, ct_strategy st, const
     to.graph_below_ms = o.graph_below_us < 0 ? -1.0 : o.graph_below_us * 1e-3;
     to.grid_modes = o.grid_modes;
     to.taps_imm = o.taps_imm;
+    to.sweep_fma2 = o.sweep_fma2;
     int threads = o.compile_threads > 0 ? o.compile_threads : (int)std::max(1u, std::thread::hardware_concurrency());
     auto* t = new ct_table();
     {
