@@ -20,12 +20,14 @@
 //                     (through L1);
 //                  1: the block stages its input tile plus halo in shared
 //                     memory, then reads windows from there
-//   CT_TMA         (chosen by the host for FP32 images with CT_SMEM = 1 when
-//                  the halo box is at most 256 x 256 elements) 1: one thread
-//                  stages the halo with a 2D tensor copy (the tensor map in
-//                  the parameter block; elements outside the image arrive as
-//                  zeros) that completes on an mbarrier.  0: every thread
-//                  copies 16-byte chunks (BF16 widened to FP32 on the way)
+//   CT_TMA         (chosen by the host with CT_SMEM = 1 when the halo box is
+//                  at most 256 x 256 elements: for FP32 images, and for BF16
+//                  images in the paired form) 1: one thread stages the halo
+//                  with a 2D tensor copy (the tensor map in the parameter
+//                  block; elements outside the image arrive as zeros) that
+//                  completes on an mbarrier; a BF16 halo stays BF16 in shared
+//                  memory and is widened as a row enters registers.  0: every
+//                  thread copies 16-byte chunks (BF16 widened to FP32 on the way)
 //   CT_UNROLL      1: fully unrolled; input rows slide through a register
 //                     window and each row feeds every output row that uses it;
 //                  0: the loop over filter rows stays rolled; 2, 4: that loop
@@ -72,8 +74,11 @@
 #ifndef CT_TMA
 #define CT_TMA 0
 #endif
-#if CT_TMA && CT_DTYPE != 0
-#error "tensor-copy staging is for FP32 images"
+#ifndef CT_FMA2
+#define CT_FMA2 0
+#endif
+#if CT_TMA && CT_DTYPE != 0 && !CT_FMA2
+#error "BF16 images are staged by a tensor copy in the paired form only"
 #endif
 // Test hook: bytes expected on top of those the tensor copy delivers; a
 // nonzero value makes the wait run out.  0 in every normal build.
@@ -87,16 +92,13 @@
 #if CT_TAPS_IMM && CT_UNROLL != 1
 #error "compiled-in taps need the unrolled body"
 #endif
-#ifndef CT_FMA2
-#define CT_FMA2 0
-#endif
 #if CT_FMA2 && (CT_UNROLL != 1 || CT_TY < 2 || CT_TAPS_IMM)
 #error "paired multiply-adds need the unrolled body, two output rows per thread and parameter-block taps"
 #endif
 #ifndef CT_SHFL
 #define CT_SHFL 0
 #endif
-#if CT_SHFL && (!CT_SMEM || CT_BX % 32 != 0 || CT_TX % 4 != 0)
+#if CT_SHFL && (!CT_SMEM || CT_BX % 32 != 0 || CT_TX % 4 != 0 || (CT_TMA && CT_DTYPE != 0))
 #error "shuffled windows need shared-memory staging, whole warps per thread row and 4-wide register tiles"
 #endif
 
@@ -144,7 +146,13 @@ struct CtParams {
 #define CT_TILE_H (CT_BY * CT_TY)
 #define CT_HALO_W (CT_TILE_W + CT_FW - 1)
 #define CT_HALO_H (CT_TILE_H + CT_FH - 1)
-#define CT_SW (((CT_HALO_W + 3) / 4) * 4)   // staged row length in floats (the tensor-copy box width)
+#if CT_TMA && CT_DTYPE != 0
+typedef ct_in_t ct_st_t;                     // the staged element: BF16 halos stay BF16
+#define CT_SW (((CT_HALO_W + 7) / 8) * 8)    // staged row length in elements (the tensor-copy box width)
+#else
+typedef float ct_st_t;
+#define CT_SW (((CT_HALO_W + 3) / 4) * 4)    // staged row length in elements (the tensor-copy box width)
+#endif
 
 #if CT_TX % 4 == 0
 #define CT_VW 4
@@ -261,6 +269,24 @@ __device__ __forceinline__ ct_u64 ct_fma2(ct_u64 a, ct_u64 b, ct_u64 c)
 }
 #endif
 
+// A staged BF16 row: VW consecutive elements per load, widened exactly.
+__device__ __forceinline__ void ct_row_shared(float (&w)[CT_WWV], const unsigned short* __restrict__ s)
+{
+#pragma unroll
+    for (int k = 0; k < CT_WWV; k += CT_VW) {
+        if (CT_VW == 4) {
+            const uint2 v = *reinterpret_cast<const uint2*>(s + k);
+            w[k] = __uint_as_float(v.x << 16); w[k + 1] = __uint_as_float(v.x & 0xffff0000u);
+            w[k + 2] = __uint_as_float(v.y << 16); w[k + 3] = __uint_as_float(v.y & 0xffff0000u);
+        } else if (CT_VW == 2) {
+            const ct_u32 v = *reinterpret_cast<const ct_u32*>(s + k);
+            w[k] = __uint_as_float(v << 16); w[k + 1] = __uint_as_float(v & 0xffff0000u);
+        } else {
+            w[k] = __uint_as_float(((ct_u32)s[k]) << 16);
+        }
+    }
+}
+
 __device__ __forceinline__ void ct_row_shared(float (&w)[CT_WWV], const float* __restrict__ s)
 {
 #pragma unroll
@@ -324,7 +350,7 @@ ct_corr2d(const __grid_constant__ CtParams p)
     __shared__ unsigned long long ct_bar;
     unsigned char* const raw = reinterpret_cast<unsigned char*>(ct_smem4);
     const unsigned mis = ct_sa(raw) & 127u;   // the tensor copy lands on a 128-byte boundary
-    float* const sm = reinterpret_cast<float*>(raw + (mis ? 128u - mis : 0u));
+    ct_st_t* const sm = reinterpret_cast<ct_st_t*>(raw + (mis ? 128u - mis : 0u));
     if (lead) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(ct_sa(&ct_bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -350,7 +376,7 @@ ct_corr2d(const __grid_constant__ CtParams p)
 #if CT_SMEM && CT_TMA
         if (lead) {
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(ct_sa(&ct_bar)),
-                         "r"((unsigned)(CT_HALO_H * CT_SW * 4 + CT_TEST_EXTRA_TX))
+                         "r"((unsigned)(CT_HALO_H * CT_SW * sizeof(ct_st_t) + CT_TEST_EXTRA_TX))
                          : "memory");
             asm volatile(
                 "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "

@@ -857,8 +857,8 @@ static ct_status run_strategy(const ct_problem& p, const Space& s, ct_strategy s
     return CT_OK;
 }
 
-// Re-measures the k fastest rows (those of at least min_ms; shorter kernels
-// keep their graph-timed figures) with `reps` launches each, interleaved
+// Re-measures the k fastest rows (unless one of them ran for less than min_ms:
+// short kernels keep their graph-timed figures) with `reps` launches each, interleaved
 // round by round so that a clock change affects every candidate alike, each
 // launch bracketed by events and preceded by the L2 flush when one is given.
 // forms bit 0: an unrolled row is also timed in its other tap form (parameter
@@ -874,13 +874,17 @@ static VariantPtr remeasure(ct_table& t, const ct_problem& p, int k, int reps, d
     std::vector<size_t> order;
     for (size_t i = 0; i < t.rows.size(); ++i) {
         const ct_row& r = t.rows[i];
-        if (r.status == CT_OK && std::isfinite(r.t_med_ms) && r.t_med_ms >= min_ms) order.push_back(i);
+        if (r.status == CT_OK && std::isfinite(r.t_med_ms)) order.push_back(i);
     }
     std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
         const ct_row &x = t.rows[a], &y = t.rows[b];
         return x.t_med_ms < y.t_med_ms || (x.t_med_ms == y.t_med_ms && x.index < y.index);
     });
     if ((int)order.size() > k) order.resize((size_t)k);
+    // short kernels keep their graph-timed figures: when any of the fastest is
+    // one, single launches would not compare with it, so nothing is re-measured
+    for (size_t i : order)
+        if (t.rows[i].t_med_ms < min_ms) return nullptr;
     if (order.size() < 2) return nullptr;
     const double t0 = now_ms();
     struct Cand {

@@ -59,7 +59,8 @@ VariantKey variant_key(const ct_problem& p, const ct_config& c, const void* h_fi
     // paired multiply-adds: unrolled, two output rows per thread, parameter-block taps
     k.cfg.fma2 = (c.fma2 && c.unroll == 1 && c.tile_y >= 2 && !c.taps) ? 1 : 0;
     // shuffled windows: staged halo, whole warps per thread row, 4-wide register tiles
-    k.cfg.shfl = (c.shfl && c.use_smem && c.block_x % 32 == 0 && c.tile_x % 4 == 0) ? 1 : 0;
+    k.cfg.shfl = (c.shfl && c.use_smem && c.block_x % 32 == 0 && c.tile_x % 4 == 0 &&
+                  !(p.dtype == CT_BF16 && k.cfg.fma2)) ? 1 : 0;
     if (!(c.taps && c.unroll == 1 && h_filter) || k.cfg.fma2) {
         k.cfg.taps = 0;
         return k;
@@ -157,13 +158,15 @@ int64_t halo_box_w(const ct_config& c, int fw, int dtype)
     return round_up((int64_t)c.block_x * c.tile_x + fw - 1, 16 / elem_size(dtype));
 }
 int64_t halo_box_h(const ct_config& c, int fh) { return (int64_t)c.block_y * c.tile_y + fh - 1; }
-// FP32 only: a BF16 halo copied as is would be widened at every window load
-// (each element is loaded by up to TY + FH - 1 rows of windows), while the
-// per-thread staging widens each element once.
+// BF16 only in the paired form: a BF16 halo copied as is is widened at every
+// window load (each element is loaded by up to TY + FH - 1 rows of windows),
+// which the scalar form pays from its issue slots (the per-thread staging
+// widens each element once instead); the paired form leaves a third of the
+// issue slots free.
 bool tma_staged(const ct_config& c, int fw, int fh, int dtype)
 {
-    return dtype == CT_F32 && c.use_smem && halo_box_w(c, fw, dtype) <= 256 && halo_box_h(c, fh) <= 256 &&
-           ((int64_t)c.block_x * c.tile_x * elem_size(dtype)) % 16 == 0;
+    return (dtype == CT_F32 || c.fma2) && c.use_smem && halo_box_w(c, fw, dtype) <= 256 &&
+           halo_box_h(c, fh) <= 256 && ((int64_t)c.block_x * c.tile_x * elem_size(dtype)) % 16 == 0;
 }
 
 unsigned* device_error_word()

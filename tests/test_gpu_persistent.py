@@ -149,3 +149,17 @@ def test_tuner_with_compiled_taps(ctlib, cuda_device):
     ref, S = oracle.corr2d_points(img, f, xs, ys)
     out, good = run_config(ctlib, d_img, f, tab.best, ow, oh)
     assert good and np.all(np.abs(out[ys, xs] - ref) <= 1e-5 * S)
+
+
+def test_remeasure_stands_down_for_graph_timed_optima(ctlib, cuda_device):
+    """A problem whose fastest kernels are timed as graphs of back-to-back
+    launches (here 256x256 / 5x5, a few microseconds each) keeps those
+    figures: nothing is re-measured by single launches, and the optimum is
+    the sweep's."""
+    p = ctlib.make_problem(256, 256, 5, 5)
+    tab = ctlib.tune(p, "small", "brute", seed=0, remeasure_top=8, remeasure_forms=3)
+    assert tab.info["remeasured"] == 0
+    assert all(not math.isfinite(r["t_remeasured_ms"]) for r in tab.rows)
+    ok = [r for r in tab.rows if r["status"] == 0]
+    best = min(ok, key=lambda r: (r["t_med_ms"], r["index"]))
+    assert tab.rows[tab.info["best_row"]]["index"] == best["index"]
