@@ -349,10 +349,11 @@ def measured_traffic(cfg_tuple, workload):
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    forms = tuple(cfg_tuple[6:8]) + (0,) * (8 - len(cfg_tuple))   # (persist, taps)
+    names = ("persist", "taps", "fma2", "shfl")
+    forms = tuple(int(v) for v in cfg_tuple[6:10]) + (0,) * max(0, 10 - len(cfg_tuple))
     for r in rec.get("captures", []):
         if (r.get("kernel_sha") == kernel_sha() and tuple(r.get("config", ())) == tuple(cfg_tuple)[:6]
-                and (int(r.get("persist", 0)), int(r.get("taps", 0))) == tuple(int(v) for v in forms)
+                and tuple(int(r.get(n, 0)) for n in names) == forms
                 and r.get("workload", "full") == workload):
             return float(r["dram_bytes_per_launch"])
     return None
