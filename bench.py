@@ -70,6 +70,8 @@ def parse():
                     help="skip: time only the batched path (profiling)")
     ap.add_argument("--batch-plain-evals", type=int, default=120,
                     help="annealing budget per filter size for the per-problem path of the batch workload")
+    ap.add_argument("--batch-bucket-forms", default="both", choices=("both", "scalar", "paired"),
+                    help="batch: bucket tiles the plan's tuner tries (scalar and/or paired multiply-adds)")
     ap.add_argument("--batch-solo-branches", type=int, default=0,
                     help="batch: parallel graph branches of the solo launches (0: library default)")
     ap.add_argument("--batch-solo-pct", type=int, default=0,
@@ -626,6 +628,11 @@ def run_ours(args):
             "n_buckets": bm["binfo"]["n_buckets"], "plan_s": bm["plan_s"], "plain_tune_s": bm["plain_tune_s"],
             "e2e_gflops": bm["flops"] / bm["te"] / 1e9, "clocks": bm["clocks"],
             "n_solo_fma2": bm["binfo"].get("n_solo_fma2"),
+            "n_paired_buckets": sum(b["config"]["fma2"] for b in bm["buckets"]),
+            "persistent_beside": bm["binfo"].get("persistent_beside"),
+            "work_interleaved": bm["binfo"].get("work_interleaved"),
+            "persistent_only_work_interleaved": bm["persistent_info"].get("work_interleaved"),
+            "persistent_only_buckets": [(b["filter"][0], b["n_items"], b["config"]) for b in bm["persistent_buckets"]],
             "plain_form_choice": bm["tuning"].get("plain_form_choice")}
         line["batched_p50_ms"] = bm["p50"]
         line["batched_p99_ms"] = bm["p99"]
@@ -767,12 +774,14 @@ def measure_batch(args, ct, dev, info, pk, fp32_peak, world, plain_cfg=None):
 
     t0 = time.time()
     batch = ct.Batch([(d_img, f, out, side + fs - 1) for (_, f, d_img, out, side, fs) in probs], tune=True,
-                     max_tune_items=6, solo_wave_pct=args.batch_solo_pct, solo_branches=args.batch_solo_branches)
+                     max_tune_items=6, solo_wave_pct=args.batch_solo_pct, solo_branches=args.batch_solo_branches,
+                     bucket_forms=args.batch_bucket_forms)
     batch_plan_s = time.time() - t0
     binfo = batch.info()
     # the same plan with every problem in the persistent launch (no solo launches)
     persistent = ct.Batch([(d_img, f, out, side + fs - 1) for (_, f, d_img, out, side, fs) in probs], tune=True,
-                          max_tune_items=6, solo_wave_pct=-1) if binfo["n_solo"] else batch
+                          max_tune_items=6, solo_wave_pct=-1,
+                          bucket_forms=args.batch_bucket_forms) if binfo["n_solo"] else batch
 
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(int(2 * max(info.l2_bytes, 64 << 20)), dtype=torch.uint8, device=dev)
@@ -856,7 +865,9 @@ def measure_batch(args, ct, dev, info, pk, fp32_peak, world, plain_cfg=None):
         "t_pg": statistics.mean(ms_plain_graph), "t_persist": statistics.mean(ms_persist),
         "identical": identical, "peak_s": peak_s, "te": te,
         "h2d": int(sum(h.numel() * 4 for h in h_imgs)), "d2h": int(sum(h.numel() * 4 for h in h_outs)),
-        "binfo": binfo, "buckets": batch.buckets(), "plan_s": batch_plan_s, "plain_tune_s": plain_tune_s,
+        "binfo": binfo, "buckets": batch.buckets(), "persistent_buckets": persistent.buckets(),
+        "persistent_info": persistent.info(),
+        "plan_s": batch_plan_s, "plain_tune_s": plain_tune_s,
         "tuning": tuning, "clocks": clocks.summary(tb0, tb1),
         # host copies of the batched outputs, for the CPU leg's check
         "results": [(img, f, snap_k[:, :side].cpu().numpy(), side, fs)
@@ -1030,6 +1041,7 @@ def run_batch(args):
         "persistent_only_ms_per_step": m["t_persist"], "persistent_only_vs_plain": t_p / m["t_persist"],
         "composite_bound_ms": m["peak_s"] * 1e3, "batched_frac_of_bound": m["peak_s"] * 1e3 / t_b,
         "batch": {"buckets": m["buckets"], **binfo, "plan_s": m["plan_s"]},
+        "persistent_only_buckets": m["persistent_buckets"], "persistent_only_info": m["persistent_info"],
         "plain_tuning": {"wall_s": m["plain_tune_s"], **m["tuning"]},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": None,

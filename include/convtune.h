@@ -456,10 +456,14 @@ CT_API ct_status ct_table_analyze(const ct_table* t, const ct_space* s, double f
  * again in the scalar and the paired multiply-add forms, on the largest such
  * problem, whose buffers the tuner uses).  The plan's graph holds these
  * launches, largest first, spread over opts->solo_branches parallel branches
- * (so small ones run beside each other), then the persistent launch of the
- * other problems.  When some solo configurations won in the paired
- * multiply-add form, the graph is captured and timed (replays, which write
- * every output) both with those and with their scalar twins, and the faster
+ * (so small ones run beside each other), and the persistent launch of the
+ * other problems, either after the solo launches or on a branch of its own
+ * beside them; its work list either takes the buckets one after another
+ * (most expensive tiles first) or interleaves them, so that tiles bound by
+ * memory bandwidth run beside tiles bound by the FMA pipe.  The graph is
+ * captured in each of these layouts and orders and, when some solo
+ * configurations won in the paired multiply-add form, also with their scalar
+ * twins; all are timed (replays, which write every output) and the fastest
  * graph is kept.
  *
  * Each item's input halo and filter taps reach shared memory by tensor-memory
@@ -485,7 +489,7 @@ typedef struct {
 typedef struct {
     int32_t block_x, block_y, tile_x, tile_y;
     int32_t unroll;          /* 1: the input-row loop is unrolled */
-    int32_t reserved;
+    int32_t fma2;            /* 1: paired multiply-adds over output-row pairs (as ct_config.fma2) */
 } ct_bucket_config;
 
 typedef struct {
@@ -501,6 +505,14 @@ typedef struct {
                                plan's graph (0: 10; < 0: every problem goes to the persistent launch) */
     int32_t solo_evals;     /* annealing budget per filter size for the solo configuration (0: 60) */
     int32_t solo_branches;  /* parallel graph branches the solo launches are spread over (0: 12) */
+    int32_t bucket_forms;   /* bucket tiles tried when tuning: 0 scalar and paired multiply-adds, 1 scalar
+                               only, 2 paired only where a tile allows it (with tune = 0: the default
+                               tile in the paired form) */
+    int32_t persistent_layout; /* the persistent launch in the graph: 0 timed both ways, the faster kept;
+                                  1 after the solo launches; 2 on a branch beside them */
+    int32_t work_order;     /* the persistent launch's work list: 0 timed both ways, the faster kept;
+                               1 bucket by bucket, most expensive tiles first; 2 buckets interleaved,
+                               each advancing through its tiles at the same relative rate */
 } ct_batch_opts;
 
 typedef struct {
@@ -511,6 +523,10 @@ typedef struct {
     double plan_ms, tune_ms, compile_cpu_ms;
     int32_t n_solo;         /* problems run as their own launch */
     int32_t n_solo_fma2;    /* of them, launches in the paired multiply-add form */
+    int32_t persistent_beside; /* 1: the persistent launch runs on a graph branch beside the solo
+                                  launches; 0: after them */
+    int32_t work_interleaved;  /* 1: the persistent launch takes its buckets' tiles interleaved; 0: bucket
+                                  by bucket */
 } ct_batch_info;
 
 typedef struct ct_batch ct_batch;

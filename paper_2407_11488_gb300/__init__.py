@@ -109,19 +109,19 @@ class BatchItem(ctypes.Structure):
 
 class BucketConfig(ctypes.Structure):
     _fields_ = [("block_x", i32), ("block_y", i32), ("tile_x", i32), ("tile_y", i32), ("unroll", i32),
-                ("reserved", i32)]
+                ("fma2", i32)]
 
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("dtype", i32), ("threads", i32), ("tune", i32), ("objective", i32), ("side_split", i32),
                 ("blocks_per_sm", i32), ("max_tune_items", i32), ("solo_wave_pct", i32), ("solo_evals", i32),
-                ("solo_branches", i32)]
+                ("solo_branches", i32), ("bucket_forms", i32), ("persistent_layout", i32), ("work_order", i32)]
 
 
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_items", i32), ("n_buckets", i32), ("n_work", i64), ("grid", i32), ("threads", i32),
                 ("smem_bytes", i32), ("regs", i32), ("plan_ms", dbl), ("tune_ms", dbl), ("compile_cpu_ms", dbl),
-                ("n_solo", i32), ("n_solo_fma2", i32)]
+                ("n_solo", i32), ("n_solo_fma2", i32), ("persistent_beside", i32), ("work_interleaved", i32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -569,7 +569,14 @@ class Batch:
     persistent launch over all problems, except those that fill at least
     ``solo_wave_pct`` percent of one wave of the GPU (0: 10; < 0: none),
     which run as their own launches of the single-problem kernel, spread over
-    ``solo_branches`` parallel graph branches (0: 12).
+    ``solo_branches`` parallel graph branches (0: 12).  ``bucket_forms``:
+    the bucket tiles tried when tuning ("both", "scalar" or "paired"
+    multiply-adds; with ``tune=False``, "paired" gives the default tile in the
+    paired form).  ``persistent_layout``: where the persistent launch sits in
+    the graph ("timed": both layouts timed, the faster kept; "after" the solo
+    launches; "beside" them, on a branch of its own).  ``work_order``: the
+    persistent launch's work list ("timed", "buckets": one bucket after
+    another, "interleaved").
 
     ``problems`` is a list of (image, filt, out, in_w): CUDA image tensor
     (in_h, in_pitch) with in_w valid columns, host filter (fh, fw), CUDA
@@ -577,7 +584,8 @@ class Batch:
     alive while the batch is used; filters are copied at creation."""
 
     def __init__(self, problems, *, dtype=None, threads=256, tune=True, objective="pp", side_split=512,
-                 blocks_per_sm=0, max_tune_items=12, solo_wave_pct=0, solo_evals=0, solo_branches=0):
+                 blocks_per_sm=0, max_tune_items=12, solo_wave_pct=0, solo_evals=0, solo_branches=0,
+                 bucket_forms="both", persistent_layout="timed", work_order="timed"):
         import torch
         self._keep = []
         arr = (BatchItem * len(problems))()
@@ -594,7 +602,10 @@ class Batch:
             arr[k] = BatchItem(img.data_ptr(), out.data_ptr(), fb.ctypes.data, p.out_w, p.out_h, p.filter_w,
                                p.filter_h, p.in_pitch, out.stride(0))
         o = BatchOpts(dt if dtype is None else dtype, threads, int(tune), 1 if objective == "time" else 0,
-                      side_split, blocks_per_sm, max_tune_items, solo_wave_pct, solo_evals, solo_branches)
+                      side_split, blocks_per_sm, max_tune_items, solo_wave_pct, solo_evals, solo_branches,
+                      {"both": 0, "scalar": 1, "paired": 2}[bucket_forms],
+                      {"timed": 0, "after": 1, "beside": 2}[persistent_layout],
+                      {"timed": 0, "buckets": 1, "interleaved": 2}[work_order])
         h = vp()
         _check(_load().ct_batch_create(arr, len(problems), ctypes.byref(o), ctypes.byref(h)))
         self.handle = h
@@ -622,7 +633,7 @@ class Batch:
             _check(_load().ct_batch_bucket(self.handle, k, ctypes.byref(fw), ctypes.byref(fh), ctypes.byref(n),
                                            ctypes.byref(c), ctypes.byref(pp)))
             res.append({"filter": (fw.value, fh.value), "n_items": n.value, "pp": pp.value,
-                        "config": {f: getattr(c, f) for f, _ in BucketConfig._fields_ if f != "reserved"}})
+                        "config": {f: getattr(c, f) for f, _ in BucketConfig._fields_}})
         return res
 
     def item_bucket(self, i: int) -> int:

@@ -34,6 +34,7 @@ std::vector<std::string> batch_options(int threads, int dtype, const std::vector
         def(p + "FW", b[k].fw);
         def(p + "FH", b[k].fh);
         def(p + "UN", b[k].cfg.un);
+        def(p + "P2", b[k].cfg.p2);
     }
     add_env_options(o);
     return o;
@@ -181,22 +182,29 @@ ct_status item_map(const ct_batch& B, int i, const TileCfg& c, unsigned char* ma
 // unrolling; the halo box must suit a tensor copy, the two item buffers must
 // leave room for min_blocks blocks per SM, and a fully unrolled body stays
 // below ~6k FMAs (instruction cache).
-std::vector<TileCfg> bucket_candidates(int threads, int fw, int fh, int dtype, int smem_limit, int min_blocks)
+// forms: 0 scalar and paired multiply-adds, 1 scalar only, 2 paired only
+// (scalar where no paired tile fits).
+std::vector<TileCfg> bucket_candidates(int threads, int fw, int fh, int dtype, int smem_limit, int min_blocks,
+                                       int forms)
 {
     std::vector<TileCfg> out;
     const int64_t cap = std::min<int64_t>(smem_limit, (int64_t)kSmemPerSM / std::max(1, min_blocks) - 1024);
     for (int bx : {16, 32, 64}) {
         if (bx > threads || threads % bx) continue;
-        for (int tx : {2, 4})
+        for (int tx : {2, 4, 8})
             for (int ty : {1, 2, 4, 8})
-                for (int un : {0, 1}) {
-                    TileCfg c{bx, tx, ty, un};
-                    if (!halo_box_ok(threads, c, fw, fh, dtype)) continue;
-                    if (bucket_smem(threads, c, fw, fh, dtype) > cap) continue;
-                    if (un && (int64_t)tx * ty * fw * (fh + ty - 1) > 6144) continue;
-                    out.push_back(c);
-                }
+                for (int un : {0, 1})
+                    for (int p2 : {0, 1}) {
+                        TileCfg c{bx, tx, ty, un, p2};
+                        if (p2 && (forms == 1 || !pair_ok(c))) continue;
+                        if (!halo_box_ok(threads, c, fw, fh, dtype)) continue;
+                        if (bucket_smem(threads, c, fw, fh, dtype) > cap) continue;
+                        if (un && (int64_t)tx * ty * fw * (fh + ty - 1) > 6144) continue;
+                        out.push_back(c);
+                    }
     }
+    if (forms == 2 && std::any_of(out.begin(), out.end(), [](const TileCfg& c) { return c.p2 != 0; }))
+        out.erase(std::remove_if(out.begin(), out.end(), [](const TileCfg& c) { return c.p2 == 0; }), out.end());
     return out;
 }
 
@@ -205,7 +213,8 @@ std::vector<TileCfg> bucket_candidates(int threads, int fw, int fh, int dtype, i
 ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o, CompilePool& pool,
                       cudaStream_t s, int smem_limit)
 {
-    std::vector<TileCfg> cand = bucket_candidates(B.threads, bk.fw, bk.fh, B.dtype, smem_limit, kMinBlocks);
+    std::vector<TileCfg> cand =
+        bucket_candidates(B.threads, bk.fw, bk.fh, B.dtype, smem_limit, kMinBlocks, o.bucket_forms);
     if (cand.empty())
         return fail(CT_ERR_INVALID_CONFIG, "no tile fits shared memory and the tensor copy for filter %dx%d", bk.fw,
                     bk.fh);
@@ -296,7 +305,7 @@ ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o,
             int64_t tx = 0;
             const int64_t nt = tiles_of(B.items[(size_t)item], B.threads, cand[ci], &tx);
             work.resize((size_t)nt);
-            for (int64_t k = 0; k < nt; ++k) work[(size_t)k] = work_item(0u, k, tx);
+            for (int64_t k = 0; k < nt; ++k) work[(size_t)k] = work_item(0u, k, tx, 0, dp.filt_off);
             cudaMemcpyAsync(d_prob, &dp, sizeof dp, cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(d_work, work.data(), (size_t)nt * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(d_map, map, kTensorMapBytes, cudaMemcpyHostToDevice, s);
@@ -476,27 +485,24 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
     B->dtype = o.dtype;
     B->threads = threads;
     B->items.assign(items, items + n);
-    // filters, widened to FP32, rows zero-padded to a multiple of 4 taps, in
-    // one arena (every filter starts on a 16-byte boundary)
-    std::vector<float> arena;
+    // filters, widened to FP32, in one arena: per filter its zero-padded tap
+    // rows and its rows of tap pairs (every filter starts on a 16-byte boundary)
+    std::vector<float> arena, f32;
     for (int i = 0; i < n; ++i) {
         const ct_batch_item& it = items[i];
-        B->filt_off.push_back((int)arena.size());
-        const int fwp = (int)round_up(it.filter_w, 4);
-        for (int r = 0; r < it.filter_h; ++r)
-            for (int c = 0; c < fwp; ++c) {
-                float v = 0.0f;
-                if (c < it.filter_w) {
-                    const int k = r * it.filter_w + c;
-                    if (o.dtype == CT_F32) {
-                        v = static_cast<const float*>(it.h_filter)[k];
-                    } else {
-                        const uint32_t u = (uint32_t) static_cast<const uint16_t*>(it.h_filter)[k] << 16;
-                        memcpy(&v, &u, 4);
-                    }
-                }
-                arena.push_back(v);
+        const int nf = it.filter_w * it.filter_h;
+        f32.resize((size_t)nf);
+        for (int k = 0; k < nf; ++k) {
+            if (o.dtype == CT_F32) {
+                f32[(size_t)k] = static_cast<const float*>(it.h_filter)[k];
+            } else {
+                const uint32_t u = (uint32_t) static_cast<const uint16_t*>(it.h_filter)[k] << 16;
+                memcpy(&f32[(size_t)k], &u, 4);
             }
+        }
+        const int64_t off = append_filter(arena, f32.data(), it.filter_w, it.filter_h);
+        if (off > (int64_t)0x7fffffff) return fail(CT_ERR_UNSUPPORTED, "filter table too large");
+        B->filt_off.push_back((int)off);
     }
     // problems that fill the GPU alone run as their own launch of the
     // single-problem kernel (constant-bank taps), configuration tuned per
@@ -551,12 +557,16 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
             if (o.tune) {
                 if ((st = tune_bucket(*B, bk, o, pool, s, smem_limit)) != CT_OK) return st;
             } else {
-                bk.cfg = TileCfg{32, 4, 4, 0};
+                // fixed default tile; bucket_forms = 2 asks for its paired form
+                bk.cfg = o.bucket_forms == 2 ? TileCfg{32, 4, 4, 1, 1} : TileCfg{32, 4, 4, 0, 0};
                 if (threads % 32) bk.cfg.bx = 16;
                 while ((bucket_smem(threads, bk.cfg, bk.fw, bk.fh, o.dtype) > smem_limit ||
                         !halo_box_ok(threads, bk.cfg, bk.fw, bk.fh, o.dtype)) &&
                        bk.cfg.ty > 1)
                     bk.cfg.ty /= 2;
+                if (bk.cfg.p2 && (!pair_ok(bk.cfg) ||
+                                  (int64_t)bk.cfg.tx * bk.cfg.ty * bk.fw * (bk.fh + bk.cfg.ty - 1) > 6144))
+                    bk.cfg = TileCfg{bk.cfg.bx, bk.cfg.tx, bk.cfg.ty, 0, 0};
                 if (!halo_box_ok(threads, bk.cfg, bk.fw, bk.fh, o.dtype))
                     return fail(CT_ERR_UNSUPPORTED, "no default tile suits a tensor copy with %d threads", threads);
             }
@@ -597,7 +607,9 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
             return (double)k.fw * k.fh * tile_w(threads, k.cfg) * tile_h(threads, k.cfg);
         };
         std::stable_sort(border.begin(), border.end(), [&](int a, int b) { return tile_cost(a) > tile_cost(b); });
+        std::vector<size_t> bstart;   // first work item of each bucket, in `border` order
         for (int b : border) {
+            bstart.push_back(work.size());
             std::vector<int> its = B->buckets[(size_t)b].items;
             std::stable_sort(its.begin(), its.end(), [&](int a, int c) {
                 return (int64_t)items[a].out_w * items[a].out_h > (int64_t)items[c].out_w * items[c].out_h;
@@ -609,12 +621,26 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
                                 (long long)kMaxTilesPerSide);
                 int64_t tx = 0;
                 const int64_t nt = tiles_of(items[i], threads, c, &tx);
-                for (int64_t k = 0; k < nt; ++k) work.push_back(work_item((uint32_t)i, k, tx));
+                for (int64_t k = 0; k < nt; ++k) work.push_back(work_item((uint32_t)i, k, tx, b, B->filt_off[(size_t)i]));
             }
         }
         if (work.size() > (size_t)0x7fffffff) return fail(CT_ERR_UNSUPPORTED, "too many tiles in one batch");
+        // second order: the buckets interleaved, each advancing through its own
+        // items at the same relative rate (item j of a bucket of m at (j + 1/2) / m),
+        // so tiles bound by memory bandwidth (small filters) run beside tiles bound
+        // by the FMA pipe (large filters) instead of after them
+        bstart.push_back(work.size());
+        std::vector<std::pair<double, size_t>> key;
+        key.reserve(work.size());
+        for (size_t q = 0; q + 1 < bstart.size(); ++q) {
+            const size_t m = bstart[q + 1] - bstart[q];
+            for (size_t j = 0; j < m; ++j) key.emplace_back(((double)j + 0.5) / (double)m, bstart[q] + j);
+        }
+        std::stable_sort(key.begin(), key.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        const size_t nw = work.size();
+        for (size_t j = 0; j < nw; ++j) work.push_back(work[key[j].second]);
     }
-    B->n_work = (int64_t)work.size();
+    B->n_work = (int64_t)(work.size() / 2);
     if ((e = cudaMalloc((void**)&B->d_counter, kCounterWords * sizeof(unsigned))) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(batch counter)");
     cudaMemsetAsync(B->d_counter, 0, kCounterWords * sizeof(unsigned), s);
@@ -632,8 +658,10 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "upload batch tables");
     if (!device_error_word()) return fail(CT_ERR_CUDA, "no device error word");   // allocated before capture
     // capture: the solo launches spread round-robin over forked streams (their
-    // ramps and tails overlap, small ones run side by side), joined, then
-    // counter reset + the persistent launch.  The fork streams and events live
+    // ramps and tails overlap, small ones run side by side), then counter
+    // reset + the persistent launch, either after all solo launches (joined)
+    // or on a branch of its own beside them (`beside`; its blocks then take
+    // SMs as the solo launches leave them).  The fork streams and events live
     // only for the capture.
     const size_t nfs = std::min<size_t>(o.solo_branches > 0 ? (size_t)o.solo_branches : 12, B->solo_items.size());
     struct Forks {
@@ -645,43 +673,53 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
             for (auto x : events) cudaEventDestroy(x);
         }
     } forks;
-    for (size_t k = 0; k < nfs + 1; ++k) {
+    for (size_t k = 0; k < nfs + 2; ++k) {
         cudaEvent_t ev = nullptr;
         if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
             return cuda_fail(e, "cudaEventCreate");
         forks.events.push_back(ev);
     }
-    for (size_t k = 0; k < nfs; ++k) {
+    for (size_t k = 0; k < nfs + 1; ++k) {
         cudaStream_t x = nullptr;
         if ((e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(e, "cudaStreamCreate");
         forks.streams.push_back(x);
     }
-    auto capture = [&](const std::vector<VariantPtr>& vars, cudaGraphExec_t* exec) -> ct_status {
+    auto capture = [&](const std::vector<VariantPtr>& vars, bool beside, int order,
+                       cudaGraphExec_t* exec) -> ct_status {
         cudaGraph_t g = nullptr;
         cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamBeginCapture");
         ct_status cst = CT_OK;
-        if (nfs > 0) {
-            cudaEventRecord(forks.events[0], s);
-            for (size_t k = 0; k < nfs; ++k) cudaStreamWaitEvent(forks.streams[k], forks.events[0], 0);
-            for (size_t k = 0; k < B->solo_items.size() && cst == CT_OK; ++k) {
-                const ct_batch_item& it = items[B->solo_items[k]];
-                const ct_problem p{it.out_w, it.out_h, it.filter_w, it.filter_h, it.in_pitch, it.out_pitch, o.dtype, 0};
-                // one block per tile: the solo launches run beside each other, and
-                // small blocks let the hardware interleave them
-                cst = launch_variant(*vars[k], p, it.d_image, it.h_filter, it.d_out, forks.streams[k % nfs], 0);
-            }
-            for (size_t k = 0; k < nfs; ++k) {
-                cudaEventRecord(forks.events[k + 1], forks.streams[k]);
-                cudaStreamWaitEvent(s, forks.events[k + 1], 0);
-            }
+        if (nfs > 0 || (beside && persistent)) cudaEventRecord(forks.events[0], s);
+        for (size_t k = 0; k < nfs; ++k) cudaStreamWaitEvent(forks.streams[k], forks.events[0], 0);
+        auto persistent_launch = [&](cudaStream_t ps) {
+            const WorkItem* wl = static_cast<const WorkItem*>(B->d_work) + (order ? B->n_work : 0);
+            DevParams prm{B->d_probs, wl, B->d_filters, B->d_tmaps, B->d_counter, (int32_t)B->n_work, 0};
+            cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned), ps);
+            return launch_batch(*B->module, B->grid, threads, prm, ps);
+        };
+        if (beside && persistent) {
+            cudaStream_t ps = forks.streams[nfs];
+            cudaStreamWaitEvent(ps, forks.events[0], 0);
+            cst = persistent_launch(ps);
         }
-        if (cst == CT_OK && persistent) {
-            DevParams prm{B->d_probs, B->d_work, B->d_filters, B->d_tmaps, B->d_counter, (int32_t)B->n_work, 0};
-            cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned), s);
-            cst = launch_batch(*B->module, B->grid, threads, prm, s);
+        for (size_t k = 0; k < B->solo_items.size() && cst == CT_OK; ++k) {
+            const ct_batch_item& it = items[B->solo_items[k]];
+            const ct_problem p{it.out_w, it.out_h, it.filter_w, it.filter_h, it.in_pitch, it.out_pitch, o.dtype, 0};
+            // one block per tile: the solo launches run beside each other, and
+            // small blocks let the hardware interleave them
+            cst = launch_variant(*vars[k], p, it.d_image, it.h_filter, it.d_out, forks.streams[k % nfs], 0);
         }
+        for (size_t k = 0; k < nfs; ++k) {
+            cudaEventRecord(forks.events[k + 1], forks.streams[k]);
+            cudaStreamWaitEvent(s, forks.events[k + 1], 0);
+        }
+        if (beside && persistent) {
+            cudaEventRecord(forks.events[nfs + 1], forks.streams[nfs]);
+            cudaStreamWaitEvent(s, forks.events[nfs + 1], 0);
+        }
+        if (cst == CT_OK && persistent && !beside) cst = persistent_launch(s);
         ce = cudaStreamEndCapture(s, &g);
         if (cst != CT_OK || ce != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -693,12 +731,14 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
         if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
         return CT_OK;
     };
-    if ((st = capture(B->solo_vars, &B->exec)) != CT_OK) return st;
-    // Solo launches in the paired multiply-add form are faster alone but may
-    // overlap worse with their neighbours: when the plan has any, the graph is
-    // also captured with their scalar twins, both graphs are timed (replays,
-    // interleaved, median of 5 after 2 warm-ups; this writes every output) and
-    // the faster is kept.
+    // Candidate graphs: solo launches in the tuned forms, and (when some won
+    // in the paired multiply-add form, which is faster alone but may overlap
+    // worse with its neighbours) with their scalar twins; each with the
+    // persistent launch after the solo launches and, when the plan has both,
+    // beside them; each with the persistent launch taking its work bucket by
+    // bucket or interleaved (when it has more than one bucket).  With more
+    // than one candidate, all are timed (replays, interleaved, median of 5
+    // after 2 warm-ups; this writes every output) and the fastest is kept.
     std::vector<VariantPtr> scalar = B->solo_vars;
     bool any_pair = false;
     for (size_t k = 0; k < scalar.size(); ++k) {
@@ -711,42 +751,72 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
             return fail(CT_ERR_COMPILE, "scalar twin of a solo variant: %s", v ? v->error.c_str() : "none");
         scalar[k] = v;
     }
-    if (any_pair) {
-        cudaGraphExec_t alt = nullptr;
-        if ((st = capture(scalar, &alt)) != CT_OK) return st;
-        cudaEvent_t ev[4];
-        for (auto& x : ev) cudaEventCreate(&x);
-        std::vector<float> ta, tb;
-        for (int r = 0; r < 7; ++r) {
-            cudaEventRecord(ev[0], s);
-            cudaGraphLaunch(B->exec, s);
-            cudaEventRecord(ev[1], s);
-            cudaGraphLaunch(alt, s);
-            cudaEventRecord(ev[2], s);
-            if ((e = cudaEventSynchronize(ev[2])) != cudaSuccess) {
-                for (auto& x : ev) cudaEventDestroy(x);
-                cudaGraphExecDestroy(alt);
-                return cuda_fail(e, "timing the batch graph forms");
+    struct Cand {
+        const std::vector<VariantPtr>* vars;
+        bool beside;
+        int order;
+        cudaGraphExec_t exec = nullptr;
+        std::vector<float> ms;
+    };
+    std::vector<Cand> cands;
+    const int n_orders = persistent && B->buckets.size() > 1 ? 2 : 1;
+    for (int form = 0; form < (any_pair ? 2 : 1); ++form)
+        for (int beside = 0; beside < (persistent && nfs > 0 ? 2 : 1); ++beside) {
+            if ((o.persistent_layout == 1 && beside) || (o.persistent_layout == 2 && !beside && nfs > 0 && persistent))
+                continue;
+            for (int order = 0; order < n_orders; ++order) {
+                if ((o.work_order == 1 && order) || (o.work_order == 2 && !order && n_orders > 1)) continue;
+                cands.push_back(Cand{form ? &scalar : &B->solo_vars, beside != 0, order});
             }
-            float a = 0.f, b = 0.f;
-            cudaEventElapsedTime(&a, ev[0], ev[1]);
-            cudaEventElapsedTime(&b, ev[1], ev[2]);
-            if (r >= 2) {
-                ta.push_back(a);
-                tb.push_back(b);
+        }
+    auto drop = [&]() {
+        for (auto& c : cands)
+            if (c.exec) cudaGraphExecDestroy(c.exec);
+    };
+    for (auto& c : cands)
+        if ((st = capture(*c.vars, c.beside, c.order, &c.exec)) != CT_OK) {
+            drop();
+            return st;
+        }
+    size_t keep = 0;
+    if (cands.size() > 1) {
+        std::vector<cudaEvent_t> ev(cands.size() + 1);
+        for (auto& x : ev) cudaEventCreate(&x);
+        e = cudaSuccess;
+        for (int r = 0; r < 7 && e == cudaSuccess; ++r) {
+            cudaEventRecord(ev[0], s);
+            for (size_t c = 0; c < cands.size(); ++c) {
+                cudaGraphLaunch(cands[c].exec, s);
+                cudaEventRecord(ev[c + 1], s);
+            }
+            if ((e = cudaEventSynchronize(ev[cands.size()])) != cudaSuccess) break;
+            for (size_t c = 0; c < cands.size() && r >= 2; ++c) {
+                float x = 0.f;
+                cudaEventElapsedTime(&x, ev[c], ev[c + 1]);
+                cands[c].ms.push_back(x);
             }
         }
         for (auto& x : ev) cudaEventDestroy(x);
-        std::sort(ta.begin(), ta.end());
-        std::sort(tb.begin(), tb.end());
-        if (tb[tb.size() / 2] < ta[ta.size() / 2]) {
-            cudaGraphExecDestroy(B->exec);
-            B->exec = alt;
-            B->solo_vars = scalar;
-        } else {
-            cudaGraphExecDestroy(alt);
+        if (e != cudaSuccess) {
+            drop();
+            return cuda_fail(e, "timing the batch graph forms");
+        }
+        double best = INFINITY;
+        for (size_t c = 0; c < cands.size(); ++c) {
+            std::sort(cands[c].ms.begin(), cands[c].ms.end());
+            const double med = cands[c].ms[cands[c].ms.size() / 2];
+            if (med < best) {
+                best = med;
+                keep = c;
+            }
         }
     }
+    B->exec = cands[keep].exec;
+    cands[keep].exec = nullptr;
+    if (cands[keep].vars == &scalar) B->solo_vars = scalar;
+    B->info.persistent_beside = cands[keep].beside ? 1 : 0;
+    B->info.work_interleaved = cands[keep].order;
+    drop();
     for (const auto& v : B->solo_vars) B->info.n_solo_fma2 += v->key.cfg.fma2 ? 1 : 0;
     B->info.n_items = n;
     B->info.n_buckets = (int32_t)B->buckets.size();
@@ -803,7 +873,7 @@ CT_API ct_status ct_batch_bucket(const ct_batch* b, int32_t k, int32_t* filter_w
     if (filter_w) *filter_w = bk.fw;
     if (filter_h) *filter_h = bk.fh;
     if (n_items) *n_items = (int32_t)bk.items.size();
-    if (cfg) *cfg = ct_bucket_config{bk.cfg.bx, b->threads / bk.cfg.bx, bk.cfg.tx, bk.cfg.ty, bk.cfg.un, 0};
+    if (cfg) *cfg = ct_bucket_config{bk.cfg.bx, b->threads / bk.cfg.bx, bk.cfg.tx, bk.cfg.ty, bk.cfg.un, bk.cfg.p2};
     if (pp) *pp = bk.pp;
     return CT_OK;
 }

@@ -21,14 +21,17 @@
 // stays BF16 in shared memory and is widened when a row enters registers),
 // CT_NB (buckets), and for every bucket b < CT_NB: CT_B<b>_BX (block width;
 // block height = CT_NT / BX), CT_B<b>_TX, CT_B<b>_TY (register tile),
-// CT_B<b>_UN (1: input-row loop unrolled), CT_B<b>_FW, CT_B<b>_FH (filter);
+// CT_B<b>_UN (1: input-row loop unrolled), CT_B<b>_P2 (1, with UN = 1 and an
+// even TY: paired multiply-adds, below), CT_B<b>_FW, CT_B<b>_FH (filter);
 // CT_MINB (blocks per SM the register allocation must allow); CT_BUF_BYTES,
 // the size of one item buffer (the largest bucket's, a multiple of 128).
 //
-// Filters are stored FP32, each row padded with zeros to a multiple of 4
-// taps, every filter starting on a 16-byte boundary.  Waits on an mbarrier
-// give up after about two seconds: the block then sets bit 0 of counter[1],
-// waits (again bounded) for the copies it started, and exits.
+// Filters are stored FP32, every filter starting on a 16-byte boundary: FH
+// rows of taps, each padded with zeros to a multiple of 4, then (for the
+// paired form) FH - 1 rows of tap pairs, row i - 1 holding (f[i][j],
+// f[i-1][j]) for j < FW, padded with zero pairs to an even count.  Waits on
+// an mbarrier give up after about two seconds: the block then sets bit 0 of
+// counter[1], waits (again bounded) for the copies it started, and exits.
 
 #ifndef CT_DTYPE
 #define CT_DTYPE 0
@@ -62,14 +65,36 @@ struct CtBatchProblem {
 
 struct CtBatchParams {
     const CtBatchProblem* probs;
-    const uint2* work;            // (problem index, (tile row << 16) | tile column)
-    const float* filters;         // all filters, FP32, rows padded to 4 taps, problem p at filt_off
+    // per work item: (problem index, (tile row << 16) | tile column, bucket,
+    // the problem's filt_off): all a block needs to stage and dispatch an
+    // item, in one 16-byte load
+    const uint4* work;
+    const float* filters;         // all filters, FP32 (layout above), problem p at filt_off
     const unsigned char* tmaps;   // problem p's tensor map (128 bytes) at tmaps + 128 p
     unsigned int* counter;        // [0]: next work item, zero before the launch; [1]: error bits
     int n_work;
 };
 
 __device__ __forceinline__ constexpr int ct_rup(int v, int m) { return (v + m - 1) / m * m; }
+
+// Two FP32 values in one 64-bit register pair, and the paired fused
+// multiply-add: d = a * b + c in each half, each half an fma.rn.f32.
+__device__ __forceinline__ ct_u64 ct_pk(float lo, float hi)
+{
+    ct_u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void ct_upk(ct_u64 r, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ ct_u64 ct_fma2(ct_u64 a, ct_u64 b, ct_u64 c)
+{
+    ct_u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
 
 __device__ __forceinline__ ct_u32 ct_sa(const void* p) { return (ct_u32)__cvta_generic_to_shared(p); }
 
@@ -139,16 +164,19 @@ __device__ __forceinline__ void ct_bulk_load(void* dst, const void* src, ct_u32 
 // inlined: each bucket's routine then gets its own register allocation and the
 // kernel needs only the largest of them, instead of the union a single inlined
 // body would hold.
-template <int BX, int TX, int TY, int FW, int FH, int UN>
+template <int BX, int TX, int TY, int FW, int FH, int UN, int P2>
 struct CtTile {
     static constexpr int BY = CT_NT / BX;
     static constexpr int TW = BX * TX, TH = BY * TY;
     static constexpr int HW = TW + FW - 1, HH = TH + FH - 1;
     static constexpr int SW = ct_rup(HW, CT_BOXQ);
     static constexpr int FWP = ct_rup(FW, 4);
+    static constexpr int FWP2 = ct_rup(FW, 2);   // tap pairs per pair row
     static constexpr int HALO_BYTES = HH * SW * CT_ESZ;
     static constexpr int TAPS_OFF = ct_rup(HALO_BYTES, 16);
-    static constexpr int TAP_BYTES = FH * FWP * 4;
+    static constexpr int PAIRS_OFF = FH * FWP * 4;   // from TAPS_OFF
+    static constexpr int TAP_BYTES = PAIRS_OFF + (P2 ? (FH - 1) * FWP2 * 8 : 0);
+    static_assert(!P2 || (UN == 1 && TY % 2 == 0), "the paired form needs an unrolled row loop and an even TY");
     static constexpr int VW = (TX % 4 == 0) ? 4 : ((TX % 2 == 0) ? 2 : 1);
     static constexpr int WW = TX + FW - 1;
     static constexpr int WWV = ct_rup(WW, VW);
@@ -157,14 +185,13 @@ struct CtTile {
     static_assert(TW % 16 == 0, "tile columns must start on 16-element boundaries");
 
     // Thread 0: starts both copies of one item into buf, completing on bar.
-    static __device__ __forceinline__ void stage(const CtBatchProblem& pr, const unsigned char* tmap,
-                                                 const float* filters, ct_u32 tile, unsigned char* buf, ct_u64* bar)
+    static __device__ __forceinline__ void stage(const unsigned char* tmap, const float* taps, ct_u32 tile,
+                                                 unsigned char* buf, ct_u64* bar)
     {
         const int gx0 = (int)(tile & 0xffffu) * TW, gy0 = (int)(tile >> 16) * TH;
-        ct_tmap_acquire(tmap);
         ct_mbar_expect_tx(bar, (ct_u32)(HALO_BYTES + TAP_BYTES + CT_TEST_EXTRA_TX));
         ct_tma_load_2d(buf, tmap, gx0, gy0, bar);
-        ct_bulk_load(buf + TAPS_OFF, filters + pr.filt_off, (ct_u32)TAP_BYTES, bar);
+        ct_bulk_load(buf + TAPS_OFF, taps, (ct_u32)TAP_BYTES, bar);
     }
 
     // Input row `row` of the thread's window, columns lx .. lx+WWV-1, as FP32.
@@ -221,6 +248,60 @@ struct CtTile {
         }
     }
 
+    // Paired form: output rows 2k and 2k+1 of the thread's tile share each
+    // input row r, with filter rows i = r - 2k and i - 1.  Where both exist,
+    // one paired multiply-add per (pair, column, tap) does both, its taps a
+    // (f[i][j], f[i-1][j]) pair from the pair rows (two pairs per 16-byte
+    // broadcast load) and its input the window value in both halves; at the
+    // two ends of a pair's input rows only one filter row exists (i = 0 for
+    // row 2k, i = FH for row 2k+1: a scalar FMA on that half).  Each output
+    // still adds its taps in (i, j) order, one fma.rn.f32 each.
+    static __device__ __forceinline__ void row_step2(const ct_in_t* halo, const float* taps, int lx, int ly, int r,
+                                                     ct_u64 (&acc2)[TY / 2][TX])
+    {
+        float w[WWV];
+        load_window(halo, ly + r, lx, w);
+        const float* pairs = taps + PAIRS_OFF / 4;
+#pragma unroll
+        for (int k = 0; k < TY / 2; ++k) {
+            const int i = r - 2 * k;
+            if (i >= 1 && i < FH) {
+#pragma unroll
+                for (int q = 0; q < FW; q += 2) {
+                    const float4 t = *reinterpret_cast<const float4*>(pairs + ((i - 1) * FWP2 + q) * 2);
+                    const ct_u64 f0 = ct_pk(t.x, t.y), f1 = ct_pk(t.z, t.w);
+#pragma unroll
+                    for (int tx = 0; tx < TX; ++tx) acc2[k][tx] = ct_fma2(ct_pk(w[tx + q], w[tx + q]), f0, acc2[k][tx]);
+                    if (q + 1 < FW) {
+#pragma unroll
+                        for (int tx = 0; tx < TX; ++tx)
+                            acc2[k][tx] = ct_fma2(ct_pk(w[tx + q + 1], w[tx + q + 1]), f1, acc2[k][tx]);
+                    }
+                }
+            } else if (i == 0 || i == FH) {
+                const int fi = i == 0 ? 0 : FH - 1;
+#pragma unroll
+                for (int q = 0; q < FW; q += 4) {
+                    const float4 t = *reinterpret_cast<const float4*>(taps + fi * FWP + q);
+                    const float f[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (q + e < FW) {
+#pragma unroll
+                            for (int tx = 0; tx < TX; ++tx) {
+                                float lo, hi;
+                                ct_upk(acc2[k][tx], lo, hi);
+                                if (i == 0) lo = fmaf(w[tx + q + e], f[e], lo);
+                                else hi = fmaf(w[tx + q + e], f[e], hi);
+                                acc2[k][tx] = ct_pk(lo, hi);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+
     // Computes and stores one item whose halo and taps are in buf.
     static __device__ __noinline__ void compute(const CtBatchProblem& pr, ct_u32 tile, const unsigned char* buf)
     {
@@ -240,7 +321,19 @@ struct CtTile {
         // as broadcast 16-byte loads.  UN = 1 unrolls the row loop (constant
         // offsets, no per-row predicates); UN = 0 keeps it rolled.  Per output
         // the taps are added in (i, j) order either way.
-        if constexpr (UN != 0) {
+        if constexpr (P2 != 0) {
+            ct_u64 acc2[TY / 2][TX];
+#pragma unroll
+            for (int k = 0; k < TY / 2; ++k)
+#pragma unroll
+                for (int tx = 0; tx < TX; ++tx) acc2[k][tx] = ct_pk(0.0f, 0.0f);
+#pragma unroll
+            for (int r = 0; r < TY + FH - 1; ++r) row_step2(halo, taps, lx, ly, r, acc2);
+#pragma unroll
+            for (int k = 0; k < TY / 2; ++k)
+#pragma unroll
+                for (int tx = 0; tx < TX; ++tx) ct_upk(acc2[k][tx], acc[2 * k][tx], acc[2 * k + 1][tx]);
+        } else if constexpr (UN != 0) {
 #pragma unroll
             for (int r = 0; r < TY + FH - 1; ++r) row_step(halo, taps, lx, ly, r, acc);
         } else {
@@ -276,17 +369,26 @@ struct CtTile {
     }
 };
 
-#define CT_TILE(b) CtTile<CT_B##b##_BX, CT_B##b##_TX, CT_B##b##_TY, CT_B##b##_FW, CT_B##b##_FH, CT_B##b##_UN>
+#define CT_TILE(b) \
+    CtTile<CT_B##b##_BX, CT_B##b##_TX, CT_B##b##_TY, CT_B##b##_FW, CT_B##b##_FH, CT_B##b##_UN, CT_B##b##_P2>
 
-// Thread 0: starts the copies of work item w into buf.
-__device__ __forceinline__ void ct_stage_item(const CtBatchParams& p, int w, unsigned char* buf, ct_u64* bar)
+// Thread 0: starts the copies of the work item `it` (its record) into buf.
+// The tensor map, written by the host before the launch, is acquired for the
+// tensor copies before this thread's first use of it; a block's items come
+// in work-list order, so a problem's map is acquired again only when the
+// thread's previous item belonged to another problem (*fenced).
+__device__ __forceinline__ void ct_stage_item(const CtBatchParams& p, uint4 it, unsigned char* buf, ct_u64* bar,
+                                              ct_u32* fenced)
 {
-    const uint2 it = p.work[w];
-    const CtBatchProblem& pr = p.probs[it.x];
     const unsigned char* tmap = p.tmaps + 128ull * it.x;
+    if (*fenced != it.x) {
+        ct_tmap_acquire(tmap);
+        *fenced = it.x;
+    }
+    const float* taps = p.filters + it.w;
 #define CT_STAGE_CASE(b) \
-    case b: CT_TILE(b)::stage(pr, tmap, p.filters, it.y, buf, bar); break;
-    switch (pr.bucket) {
+    case b: CT_TILE(b)::stage(tmap, taps, it.y, buf, bar); break;
+    switch (it.z) {
 #if CT_NB > 0
     CT_STAGE_CASE(0)
 #endif
@@ -340,11 +442,12 @@ __device__ __forceinline__ void ct_stage_item(const CtBatchParams& p, int w, uns
 #undef CT_STAGE_CASE
 }
 
-__device__ __forceinline__ void ct_compute_item(const CtBatchProblem& pr, ct_u32 tile, const unsigned char* buf)
+__device__ __forceinline__ void ct_compute_item(const CtBatchProblem& pr, ct_u32 tile, ct_u32 bucket,
+                                                const unsigned char* buf)
 {
 #define CT_COMPUTE_CASE(b) \
     case b: CT_TILE(b)::compute(pr, tile, buf); break;
-    switch (pr.bucket) {
+    switch (bucket) {
 #if CT_NB > 0
     CT_COMPUTE_CASE(0)
 #endif
@@ -399,9 +502,12 @@ __device__ __forceinline__ void ct_compute_item(const CtBatchProblem& pr, ct_u32
 }
 
 // Persistent loop, two item buffers: while item k is computed from one, the
-// copies of item k+1 into the other are in flight.  Work indices rotate
-// through three shared slots, so the slot thread 0 overwrites was last read
-// two barriers earlier.
+// copies of item k+1 into the other are in flight.  Work indices and item
+// records rotate through three shared slots, so the slot thread 0 overwrites
+// was last read two barriers earlier.  Thread 0 keeps the fetches off the
+// block's critical path: the atomic that claims item k+2 is issued while
+// item k starts (its result is first needed one item later), and item k+1's
+// record is loaded before the barrier that precedes its staging.
 #ifndef CT_MINB
 #define CT_MINB 1
 #endif
@@ -410,37 +516,53 @@ extern "C" __global__ void __launch_bounds__(CT_NT, CT_MINB) ct_corr2d_batch(con
     extern __shared__ float4 ct_smem4[];
     __shared__ ct_u64 s_bar[2];
     __shared__ int s_w[3];
+    __shared__ uint4 s_it[3];
     unsigned char* const raw = reinterpret_cast<unsigned char*>(ct_smem4);
     const ct_u32 mis = ct_sa(raw) & 127u;   // tensor copies land on 128-byte boundaries
     unsigned char* const buf0 = raw + (mis ? 128u - mis : 0u);
     unsigned char* const buf1 = buf0 + CT_BUF_BYTES;
     const int tid = threadIdx.x;
+    ct_u32 fenced = 0xffffffffu;   // thread 0: problem whose tensor map it acquired last
+    int claimed = 0;               // thread 0: index claimed for the item after next
     if (tid == 0) {
         ct_mbar_init(&s_bar[0], 1u);
         ct_mbar_init(&s_bar[1], 1u);
         ct_mbar_init_fence();
-        s_w[0] = (int)atomicAdd(p.counter, 1u);
+        const int w0 = (int)atomicAdd(p.counter, 1u);
+        s_w[0] = w0;
+        if (w0 < p.n_work) {
+            const uint4 it = p.work[w0];
+            s_it[0] = it;
+            ct_stage_item(p, it, buf0, &s_bar[0], &fenced);
+        }
+        claimed = (int)atomicAdd(p.counter, 1u);
     }
     __syncthreads();
     ct_u32 phase = 0u;     // bit b: parity of buffer b's next completion
-    ct_u32 pending = 0u;   // bit b: copies into buffer b started and not yet waited for
+    ct_u32 pending = s_w[0] < p.n_work ? 1u : 0u;   // bit b: copies into buffer b started, not yet waited for
     int failed = 0;
-    if (s_w[0] < p.n_work) {
-        if (tid == 0) ct_stage_item(p, s_w[0], buf0, &s_bar[0]);
-        pending = 1u;
-    }
     int slot = 0;   // s_w[slot] holds item k's index
     for (int k = 0;; ++k) {
         const int cur = k & 1, nxt = cur ^ 1;
         const int nslot = slot == 2 ? 0 : slot + 1;
-        if (tid == 0) s_w[nslot] = (int)atomicAdd(p.counter, 1u);
+        uint4 it_next = make_uint4(0u, 0u, 0u, 0u);
+        if (tid == 0) {
+            const int wn = claimed;
+            s_w[nslot] = wn;
+            if (wn < p.n_work) it_next = p.work[wn];
+            if (wn < p.n_work) claimed = (int)atomicAdd(p.counter, 1u);
+        }
         // next index visible; every thread is done with the other buffer;
         // a timed-out wait in any thread stops the block
         if (__syncthreads_or(failed)) break;
         const int w = s_w[slot], wn = s_w[nslot];
+        const int my = slot;
         slot = nslot;
         if (wn < p.n_work) {
-            if (tid == 0) ct_stage_item(p, wn, nxt ? buf1 : buf0, &s_bar[nxt]);
+            if (tid == 0) {
+                s_it[nslot] = it_next;
+                ct_stage_item(p, it_next, nxt ? buf1 : buf0, &s_bar[nxt], &fenced);
+            }
             pending |= 1u << nxt;
         }
         if (w >= p.n_work) break;
@@ -452,8 +574,8 @@ extern "C" __global__ void __launch_bounds__(CT_NT, CT_MINB) ct_corr2d_batch(con
             failed = 1;
             continue;
         }
-        const uint2 it = p.work[w];
-        ct_compute_item(p.probs[it.x], it.y, cur ? buf1 : buf0);
+        const uint4 it = s_it[my];
+        ct_compute_item(p.probs[it.x], it.y, it.z, cur ? buf1 : buf0);
     }
     // copies can still be in flight only after a timed-out wait
     for (int b = 0; b < 2; ++b)

@@ -12,6 +12,7 @@ namespace ct {
 
 struct TileCfg {
     int bx = 32, tx = 4, ty = 4, un = 0;
+    int p2 = 0;   // 1: paired multiply-adds over output-row pairs (needs un = 1 and an even ty)
 };
 
 // Mirrors of the device structs in batch.cuh.
@@ -35,14 +36,18 @@ struct DevParams {
 static_assert(sizeof(DevParams) == 48, "DevParams layout");
 constexpr int kCounterWords = 2;
 // One tile of one problem; the tile is (row << 16) | column, so the kernel
-// places it without a division.
+// places it without a division.  The record also carries the problem's
+// bucket and filter offset, so a block stages and dispatches an item after
+// one 16-byte load.
 struct WorkItem {
-    uint32_t problem, tile;
+    uint32_t problem, tile, bucket, filt_off;
 };
+static_assert(sizeof(WorkItem) == 16, "WorkItem layout");
 constexpr int64_t kMaxTilesPerSide = 65535;
-inline WorkItem work_item(uint32_t problem, int64_t k, int64_t tiles_x)
+inline WorkItem work_item(uint32_t problem, int64_t k, int64_t tiles_x, int32_t bucket, int32_t filt_off)
 {
-    return WorkItem{problem, (uint32_t)(((k / tiles_x) << 16) | (k % tiles_x))};
+    return WorkItem{problem, (uint32_t)(((k / tiles_x) << 16) | (k % tiles_x)), (uint32_t)bucket,
+                    (uint32_t)filt_off};
 }
 inline bool tile_grid_ok(int64_t out_w, int64_t out_h, int64_t tw, int64_t th)
 {
@@ -73,11 +78,38 @@ inline bool halo_box_ok(int threads, const TileCfg& c, int fw, int fh, int dtype
            tile_w(threads, c) % 16 == 0;
 }
 
-// bytes of one item buffer (halo box, then taps), a multiple of 128
+// Floats of one filter in the batch's filter table: fh rows of taps padded
+// to a multiple of 4, then fh - 1 rows of (f[i][j], f[i-1][j]) pairs padded
+// to an even count (read by buckets in the paired form).  Both parts are
+// multiples of 4 floats, so every filter starts on a 16-byte boundary.
+inline int64_t filter_rows_floats(int fw, int fh) { return (int64_t)fh * round_up(fw, 4); }
+inline int64_t filter_pairs_floats(int fw, int fh) { return (int64_t)(fh - 1) * round_up(fw, 2) * 2; }
+
+// Appends one FP32 filter (fh x fw, row-major) to a batch filter table in the
+// layout above; returns its offset in floats.
+inline int64_t append_filter(std::vector<float>& table, const float* f, int fw, int fh)
+{
+    const int64_t off = (int64_t)table.size();
+    const int fwp = (int)round_up(fw, 4), fwp2 = (int)round_up(fw, 2);
+    for (int i = 0; i < fh; ++i)
+        for (int j = 0; j < fwp; ++j) table.push_back(j < fw ? f[i * fw + j] : 0.0f);
+    for (int i = 1; i < fh; ++i)
+        for (int j = 0; j < fwp2; ++j) {
+            table.push_back(j < fw ? f[i * fw + j] : 0.0f);
+            table.push_back(j < fw ? f[(i - 1) * fw + j] : 0.0f);
+        }
+    return off;
+}
+
+// Whether a bucket tile can take the paired form.
+inline bool pair_ok(const TileCfg& c) { return c.un == 1 && c.ty >= 2 && c.ty % 2 == 0; }
+
+// bytes of one item buffer (halo box, then taps and, paired, tap pairs), a multiple of 128
 inline int64_t bucket_buf_bytes(int threads, const TileCfg& c, int fw, int fh, int dtype)
 {
     const int64_t halo = batch_box_w(threads, c, fw, dtype) * batch_box_h(threads, c, fh) * elem_size(dtype);
-    return round_up(round_up(halo, 16) + (int64_t)fh * round_up(fw, 4) * 4, 128);
+    const int64_t taps = 4 * (filter_rows_floats(fw, fh) + (c.p2 ? filter_pairs_floats(fw, fh) : 0));
+    return round_up(round_up(halo, 16) + taps, 128);
 }
 
 // dynamic shared memory of the kernel: two item buffers plus alignment slack

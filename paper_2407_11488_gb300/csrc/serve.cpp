@@ -378,7 +378,7 @@ bool ct_server::launch_locked(Launch& L)
         }
         memcpy(filt + toff, r.taps.data(), r.taps.size() * 4);
         toff += r.taps.size();
-        for (int64_t k = 0; k < nt; ++k) work[w++] = work_item((uint32_t)i, k, tx);
+        for (int64_t k = 0; k < nt; ++k) work[w++] = work_item((uint32_t)i, k, tx, d.bucket, d.filt_off);
     }
     unsigned char* dt = base + tab_off;
     cudaMemcpyAsync(dt, st, tab_bytes, cudaMemcpyHostToDevice, L.stream);

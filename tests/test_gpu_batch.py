@@ -47,12 +47,26 @@ SHAPES = [(700, 650, 17, 17), (513, 300, 11, 11), (128, 128, 3, 3), (1, 1, 5, 5)
           (64, 64, 17, 17), (1024, 200, 7, 7)]
 
 
-@pytest.mark.parametrize("tune", [True, False])
-def test_batch_matches_oracle_and_single_kernel(ctlib, cuda_device, tune):
+@pytest.mark.parametrize("tune,forms,order", [(True, "both", "timed"), (False, "both", "buckets"),
+                                              (True, "paired", "interleaved"), (False, "paired", "interleaved")])
+def test_batch_matches_oracle_and_single_kernel(ctlib, cuda_device, tune, forms, order):
+    """forms = "paired": every bucket tile that allows it runs paired
+    multiply-adds over output-row pairs (filters of 1, 2 and more rows, odd
+    and even widths), with the same bits as the scalar single-problem kernel.
+    order: the persistent launch's work list bucket by bucket, interleaved,
+    or whichever timed faster."""
     probs = _make(SHAPES, 3, cuda_device)
     b = ctlib.Batch([(d, f, out, ow + fw - 1) for (_, f, d, out, ow, oh, fw, fh) in probs], tune=tune,
-                    max_tune_items=4, solo_wave_pct=-1)        # every problem in the persistent launch
+                    max_tune_items=4, solo_wave_pct=-1, bucket_forms=forms,
+                    work_order=order)   # every problem in the persistent launch
     info = b.info()
+    assert info["work_interleaved"] == {"buckets": 0, "interleaved": 1}.get(order, info["work_interleaved"])
+    if forms == "paired":
+        paired = [bk for bk in b.buckets() if bk["config"]["fma2"]]
+        assert len(paired) >= len(b.buckets()) - 1, b.buckets()
+        assert any(bk["filter"][1] == 1 for bk in paired) and any(bk["filter"] == (17, 17) for bk in paired)
+        for bk in paired:
+            assert bk["config"]["unroll"] == 1 and bk["config"]["tile_y"] % 2 == 0
     assert info["n_items"] == len(SHAPES) and info["n_work"] > 0 and info["grid"] > 0
     for rep in range(2):       # the graph is replayable
         b.run()
@@ -77,11 +91,14 @@ def test_batch_matches_oracle_and_single_kernel(ctlib, cuda_device, tune):
         assert b.buckets()[b.item_bucket(i)]["filter"] == (fw, fh)
 
 
-def test_batch_bf16(ctlib, cuda_device):
+@pytest.mark.parametrize("forms", ["both", "paired"])
+def test_batch_bf16(ctlib, cuda_device, forms):
     shapes = [(300, 200, 9, 9), (1024, 64, 17, 17), (50, 77, 3, 5)]
     probs = _make(shapes, 4, cuda_device, dtype=torch.bfloat16)
     b = ctlib.Batch([(d, f, out, ow + fw - 1) for (_, f, d, out, ow, oh, fw, fh) in probs], tune=False,
-                    solo_wave_pct=-1)
+                    solo_wave_pct=-1, bucket_forms=forms)
+    if forms == "paired":
+        assert all(bk["config"]["fma2"] for bk in b.buckets())
     b.run()
     torch.cuda.synchronize()
     b.check()
@@ -157,19 +174,22 @@ def test_wait_timeout_is_reported(ctlib, cuda_device, monkeypatch):
     assert_parity(out[:oh, :ow].cpu().numpy(), ref, S, "batch after a timed-out run")
 
 
-def test_solo_problems_in_the_graph(ctlib, cuda_device):
+@pytest.mark.parametrize("layout", ["timed", "after", "beside"])
+def test_solo_problems_in_the_graph(ctlib, cuda_device, layout):
     """A problem that fills the GPU on its own (here: one wave) runs as its
     own tuned single-problem launch in the plan's graph, the others in the
-    persistent launch; all outputs are bit-identical to the single-problem
-    kernel and match the oracle (sampled for the big one).  4500^2 outputs
-    exceed one wave under every configuration of the space (at most 65,536
-    outputs per block, at most 2,048 threads per SM)."""
+    persistent launch (after the solo launch, beside it, or whichever timed
+    faster); all outputs are bit-identical to the single-problem kernel and
+    match the oracle (sampled for the big one).  4500^2 outputs exceed one
+    wave under every configuration of the space (at most 65,536 outputs per
+    block, at most 2,048 threads per SM)."""
     shapes = [(4500, 4500, 17, 17), (300, 200, 17, 17), (513, 300, 11, 11), (64, 64, 3, 3)]
     probs = _make(shapes, 12, cuda_device)
     b = ctlib.Batch([(d, f, out, ow + fw - 1) for (_, f, d, out, ow, oh, fw, fh) in probs], tune=True,
-                    max_tune_items=3, solo_wave_pct=100, solo_evals=12)
+                    max_tune_items=3, solo_wave_pct=100, solo_evals=12, persistent_layout=layout)
     info = b.info()
     assert info["n_solo"] == 1 and b.item_bucket(0) == -1
+    assert info["persistent_beside"] == {"after": 0, "beside": 1}.get(layout, info["persistent_beside"])
     assert all(b.item_bucket(i) >= 0 for i in range(1, len(shapes)))
     for rep in range(2):
         b.run()
