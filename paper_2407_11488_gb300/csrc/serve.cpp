@@ -484,6 +484,9 @@ CT_API ct_status ct_server_create(const ct_server_opts* opts, ct_server** out)
         bo.tune = 1;
         bo.side_split = -1;
         bo.solo_wave_pct = -1;   // every representative problem tunes its bucket
+        // scalar tiles only: requests bring their taps in the plain row layout,
+        // and the served launches are bound by host work, not by the FMA pipe
+        bo.bucket_forms = 1;
         ct_batch* tb = nullptr;
         st = ct_batch_create(items.data(), (int32_t)items.size(), &bo, &tb);
         if (st == CT_OK) {
