@@ -69,7 +69,8 @@ def parse():
     ap.add_argument("--batch-plain", choices=["tune", "skip"], default="tune",
                     help="skip: time only the batched path (profiling)")
     ap.add_argument("--batch-plain-evals", type=int, default=120,
-                    help="annealing budget per filter size for the per-problem path of the batch workload")
+                    help="annealing budget per filter size for the per-problem path of the batch workload "
+                         "and for the batch plan's solo launches (the same budget on both sides)")
     ap.add_argument("--batch-bucket-forms", default="both", choices=("both", "scalar", "paired"),
                     help="batch: bucket tiles the plan's tuner tries (scalar and/or paired multiply-adds)")
     ap.add_argument("--batch-solo-branches", type=int, default=0,
@@ -775,7 +776,7 @@ def measure_batch(args, ct, dev, info, pk, fp32_peak, world, plain_cfg=None):
     t0 = time.time()
     batch = ct.Batch([(d_img, f, out, side + fs - 1) for (_, f, d_img, out, side, fs) in probs], tune=True,
                      max_tune_items=6, solo_wave_pct=args.batch_solo_pct, solo_branches=args.batch_solo_branches,
-                     bucket_forms=args.batch_bucket_forms)
+                     solo_evals=args.batch_plain_evals, bucket_forms=args.batch_bucket_forms)
     batch_plan_s = time.time() - t0
     binfo = batch.info()
     # the same plan with every problem in the persistent launch (no solo launches)
