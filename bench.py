@@ -75,6 +75,8 @@ def parse():
                          "and for the batch plan's solo launches (the same budget on both sides)")
     ap.add_argument("--batch-bucket-forms", default="both", choices=("both", "scalar", "paired"),
                     help="batch: bucket tiles the plan's tuner tries (scalar and/or paired multiply-adds)")
+    ap.add_argument("--batch-min-blocks", type=int, default=0,
+                    help="batch: resident blocks per SM the persistent kernel is built for (0: library default)")
     ap.add_argument("--batch-solo-branches", type=int, default=0,
                     help="batch: parallel graph branches of the solo launches (0: library default)")
     ap.add_argument("--batch-solo-pct", type=int, default=0,
@@ -801,13 +803,14 @@ def measure_batch(args, ct, dev, info, pk, fp32_peak, world, plain_cfg=None):
     t0 = time.time()
     batch = ct.Batch([(d_img, f, out, side + fs - 1) for (_, f, d_img, out, side, fs) in probs], tune=True,
                      max_tune_items=6, solo_wave_pct=args.batch_solo_pct, solo_branches=args.batch_solo_branches,
-                     solo_evals=args.batch_plain_evals, bucket_forms=args.batch_bucket_forms)
+                     solo_evals=args.batch_plain_evals, bucket_forms=args.batch_bucket_forms,
+                     min_blocks_per_sm=args.batch_min_blocks)
     batch_plan_s = time.time() - t0
     binfo = batch.info()
     # the same plan with every problem in the persistent launch (no solo launches)
     persistent = ct.Batch([(d_img, f, out, side + fs - 1) for (_, f, d_img, out, side, fs) in probs], tune=True,
-                          max_tune_items=6, solo_wave_pct=-1,
-                          bucket_forms=args.batch_bucket_forms) if binfo["n_solo"] else batch
+                          max_tune_items=6, solo_wave_pct=-1, bucket_forms=args.batch_bucket_forms,
+                          min_blocks_per_sm=args.batch_min_blocks) if binfo["n_solo"] else batch
 
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(int(2 * max(info.l2_bytes, 64 << 20)), dtype=torch.uint8, device=dev)

@@ -513,6 +513,9 @@ typedef struct {
     int32_t work_order;     /* the persistent launch's work list: 0 timed both ways, the faster kept;
                                1 bucket by bucket, most expensive tiles first; 2 buckets interleaved,
                                each advancing through its tiles at the same relative rate */
+    int32_t min_blocks_per_sm; /* resident blocks per SM the persistent kernel's registers must allow
+                                  (1..8; 0: 4); bucket tiles whose two item buffers do not fit that
+                                  many blocks' share of shared memory are not tried */
 } ct_batch_opts;
 
 typedef struct {

@@ -115,7 +115,8 @@ class BucketConfig(ctypes.Structure):
 class BatchOpts(ctypes.Structure):
     _fields_ = [("dtype", i32), ("threads", i32), ("tune", i32), ("objective", i32), ("side_split", i32),
                 ("blocks_per_sm", i32), ("max_tune_items", i32), ("solo_wave_pct", i32), ("solo_evals", i32),
-                ("solo_branches", i32), ("bucket_forms", i32), ("persistent_layout", i32), ("work_order", i32)]
+                ("solo_branches", i32), ("bucket_forms", i32), ("persistent_layout", i32), ("work_order", i32),
+                ("min_blocks_per_sm", i32)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -576,7 +577,8 @@ class Batch:
     the graph ("timed": both layouts timed, the faster kept; "after" the solo
     launches; "beside" them, on a branch of its own).  ``work_order``: the
     persistent launch's work list ("timed", "buckets": one bucket after
-    another, "interleaved").
+    another, "interleaved").  ``min_blocks_per_sm``: resident blocks per SM
+    the persistent kernel is built for (0: 4).
 
     ``problems`` is a list of (image, filt, out, in_w): CUDA image tensor
     (in_h, in_pitch) with in_w valid columns, host filter (fh, fw), CUDA
@@ -585,7 +587,7 @@ class Batch:
 
     def __init__(self, problems, *, dtype=None, threads=256, tune=True, objective="pp", side_split=512,
                  blocks_per_sm=0, max_tune_items=12, solo_wave_pct=0, solo_evals=0, solo_branches=0,
-                 bucket_forms="both", persistent_layout="timed", work_order="timed"):
+                 bucket_forms="both", persistent_layout="timed", work_order="timed", min_blocks_per_sm=0):
         import torch
         self._keep = []
         arr = (BatchItem * len(problems))()
@@ -605,7 +607,7 @@ class Batch:
                       side_split, blocks_per_sm, max_tune_items, solo_wave_pct, solo_evals, solo_branches,
                       {"both": 0, "scalar": 1, "paired": 2}[bucket_forms],
                       {"timed": 0, "after": 1, "beside": 2}[persistent_layout],
-                      {"timed": 0, "buckets": 1, "interleaved": 2}[work_order])
+                      {"timed": 0, "buckets": 1, "interleaved": 2}[work_order], min_blocks_per_sm)
         h = vp()
         _check(_load().ct_batch_create(arr, len(problems), ctypes.byref(o), ctypes.byref(h)))
         self.handle = h

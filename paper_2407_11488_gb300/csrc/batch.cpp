@@ -15,14 +15,14 @@ static const char kBatchSource[] =
 #include "batch_src.inc"
     ;
 
-std::vector<std::string> batch_options(int threads, int dtype, const std::vector<BucketDesc>& b)
+std::vector<std::string> batch_options(int threads, int dtype, const std::vector<BucketDesc>& b, int min_blocks)
 {
     std::vector<std::string> o = nvrtc_base_options();
     auto def = [&](const std::string& n, int v) { o.push_back("-D" + n + "=" + std::to_string(v)); };
     def("CT_NT", threads);
     def("CT_DTYPE", dtype);
     def("CT_NB", (int)b.size());
-    def("CT_MINB", kMinBlocks);
+    def("CT_MINB", min_blocks);
     int64_t buf = 128;
     for (const auto& d : b) buf = std::max(buf, bucket_buf_bytes(threads, d.cfg, d.fw, d.fh, dtype));
     def("CT_BUF_BYTES", (int)buf);
@@ -51,10 +51,11 @@ uint64_t options_key(const std::vector<std::string>& o)
     return h;
 }
 
-VariantPtr compile_batch(int threads, int dtype, const std::vector<BucketDesc>& b, const std::string& dir)
+VariantPtr compile_batch(int threads, int dtype, const std::vector<BucketDesc>& b, const std::string& dir,
+                         int min_blocks)
 {
-    VariantPtr v = compile_source(kBatchSource, sizeof kBatchSource, "batch.cu", batch_options(threads, dtype, b),
-                                  "ct_corr2d_batch", dir);
+    VariantPtr v = compile_source(kBatchSource, sizeof kBatchSource, "batch.cu",
+                                  batch_options(threads, dtype, b, min_blocks), "ct_corr2d_batch", dir);
     int64_t sm = 0;
     for (const auto& d : b) sm = std::max(sm, bucket_smem(threads, d.cfg, d.fw, d.fh, dtype));
     v->smem = sm;
@@ -103,7 +104,7 @@ struct ct_batch {
         TileCfg cfg;
         double pp = NAN;
     };
-    int dtype = CT_F32, threads = 256;
+    int dtype = CT_F32, threads = 256, min_blocks = kMinBlocks;
     std::vector<ct_batch_item> items;
     std::vector<int> item_bucket;
     std::vector<int> filt_off;
@@ -214,7 +215,7 @@ ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o,
                       cudaStream_t s, int smem_limit)
 {
     std::vector<TileCfg> cand =
-        bucket_candidates(B.threads, bk.fw, bk.fh, B.dtype, smem_limit, kMinBlocks, o.bucket_forms);
+        bucket_candidates(B.threads, bk.fw, bk.fh, B.dtype, smem_limit, B.min_blocks, o.bucket_forms);
     if (cand.empty())
         return fail(CT_ERR_INVALID_CONFIG, "no tile fits shared memory and the tensor copy for filter %dx%d", bk.fw,
                     bk.fh);
@@ -252,11 +253,11 @@ ct_status tune_bucket(ct_batch& B, ct_batch::Bucket& bk, const ct_batch_opts& o,
     std::vector<uint64_t> keys;
     for (const auto& c : cand) {
         std::vector<BucketDesc> one = {{bk.fw, bk.fh, c}};
-        const uint64_t key = options_key(batch_options(B.threads, B.dtype, one));
+        const uint64_t key = options_key(batch_options(B.threads, B.dtype, one, B.min_blocks));
         const std::string dir = pool.cache_dir();
-        const int thr = B.threads, dt = B.dtype;
+        const int thr = B.threads, dt = B.dtype, mb = B.min_blocks;
         keys.push_back(key);
-        futs.push_back(pool.request(key, [thr, dt, one, dir] { return compile_batch(thr, dt, one, dir); }));
+        futs.push_back(pool.request(key, [thr, dt, one, dir, mb] { return compile_batch(thr, dt, one, dir, mb); }));
     }
     int64_t max_tiles = 1;
     for (const auto& c : cand)
@@ -471,6 +472,8 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
     if (o.dtype != CT_F32 && o.dtype != CT_BF16) return fail(CT_ERR_INVALID_ARG, "bad batch dtype %d", o.dtype);
     const int threads = o.threads > 0 ? o.threads : 256;
     if (threads % 16 || threads > 1024) return fail(CT_ERR_INVALID_ARG, "threads must be a multiple of 16, <= 1024");
+    if (o.min_blocks_per_sm < 0 || o.min_blocks_per_sm > 8)
+        return fail(CT_ERR_INVALID_ARG, "min_blocks_per_sm must be 0..8");
     const int split = o.side_split == 0 ? 512 : o.side_split;
     ct_status st;
     for (int i = 0; i < n; ++i) {
@@ -484,6 +487,7 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
     auto B = std::unique_ptr<ct_batch>(new ct_batch());
     B->dtype = o.dtype;
     B->threads = threads;
+    B->min_blocks = o.min_blocks_per_sm > 0 ? o.min_blocks_per_sm : kMinBlocks;
     B->items.assign(items, items + n);
     // filters, widened to FP32, in one arena: per filter its zero-padded tap
     // rows and its rows of tap pairs (every filter starts on a 16-byte boundary)
@@ -581,7 +585,7 @@ CT_API ct_status ct_batch_create(const ct_batch_item* items, int32_t n, const ct
         // the persistent kernel with every bucket's tile routine
         std::vector<BucketDesc> desc;
         for (const auto& bk : B->buckets) desc.push_back({bk.fw, bk.fh, bk.cfg});
-        B->module = compile_batch(threads, o.dtype, desc, cache_dir_setting());
+        B->module = compile_batch(threads, o.dtype, desc, cache_dir_setting(), B->min_blocks);
         compile_cpu += B->module->compile_ms;
         if (B->module->status != CT_OK) return fail(CT_ERR_COMPILE, "%s", B->module->error.c_str());
         if (B->module->smem > smem_limit)

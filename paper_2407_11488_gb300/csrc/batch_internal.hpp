@@ -118,11 +118,15 @@ inline int64_t bucket_smem(int threads, const TileCfg& c, int fw, int fh, int dt
     return 2 * bucket_buf_bytes(threads, c, fw, fh, dtype) + 128;
 }
 
-std::vector<std::string> batch_options(int threads, int dtype, const std::vector<BucketDesc>& b);
+// min_blocks: resident blocks per SM the register allocation must allow
+// (__launch_bounds__ minimum), kMinBlocks unless a plan asks otherwise.
+std::vector<std::string> batch_options(int threads, int dtype, const std::vector<BucketDesc>& b,
+                                       int min_blocks = kMinBlocks);
 
 uint64_t options_key(const std::vector<std::string>& o);
 
-VariantPtr compile_batch(int threads, int dtype, const std::vector<BucketDesc>& b, const std::string& dir);
+VariantPtr compile_batch(int threads, int dtype, const std::vector<BucketDesc>& b, const std::string& dir,
+                         int min_blocks = kMinBlocks);
 
 ct_status launch_batch(Variant& v, int grid, int threads, const DevParams& prm, cudaStream_t s);
 
