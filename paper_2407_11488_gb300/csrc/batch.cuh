@@ -523,7 +523,7 @@ extern "C" __global__ void __launch_bounds__(CT_NT, CT_MINB) ct_corr2d_batch(con
     unsigned char* const buf1 = buf0 + CT_BUF_BYTES;
     const int tid = threadIdx.x;
     ct_u32 fenced = 0xffffffffu;   // thread 0: problem whose tensor map it acquired last
-    int claimed = 0;               // thread 0: index claimed for the item after next
+    int claimed = 0;               // thread 0: the last index claimed (item k+1's at the top of iteration k)
     if (tid == 0) {
         ct_mbar_init(&s_bar[0], 1u);
         ct_mbar_init(&s_bar[1], 1u);
