@@ -335,6 +335,12 @@ def test_batch_validation_without_gpu(ctlib):
     st = ctlib.lib().ct_batch_create(items, 1, None, ctypes.byref(h))
     assert st == -1 and b"item 0" in ctlib.lib().ct_last_error()
     assert ctlib.lib().ct_batch_create(items, 0, None, ctypes.byref(h)) == -1
+    good = (ctlib.BatchItem * 1)()
+    good[0] = ctlib.BatchItem(16, 16, 16, 64, 64, 5, 5, 68, 64)
+    for field, bad in (("min_blocks_per_sm", 9), ("min_blocks_per_sm", -1), ("threads", 100)):
+        o = ctlib.BatchOpts()
+        setattr(o, field, bad)
+        assert ctlib.lib().ct_batch_create(good, 1, ctypes.byref(o), ctypes.byref(h)) == -1, field
     if NO_GPU:
         items[0] = ctlib.BatchItem(16, 16, 16, 64, 64, 5, 5, 68, 64)
         assert ctlib.lib().ct_batch_create(items, 1, None, ctypes.byref(h)) == -8
